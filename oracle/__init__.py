@@ -1,0 +1,346 @@
+"""FP64 CPU oracle of the FOSB hot path (PEC EFIE, RWG, combination technique).
+
+TEST INFRASTRUCTURE ONLY: the slow, plain reference the CUDA library is checked
+against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg import it; the library never does, and the two share no code.  The
+seeded mesh generators of ``fosb_synth`` feed both sides.
+
+Every function states the passage of the paper it follows.  Quadrature loops live in
+``efie_oracle.cpp`` (plain C++, one point pair at a time); the dense linear algebra
+uses numpy/LAPACK as a library primitive (``numpy.linalg.solve``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C++ quadrature core with g++ (OpenMP over test triangles)."""
+    src = os.path.join(_HERE, "efie_oracle.cpp")
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.orc_ss_integral.restype = ctypes.c_double
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def n_threads() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+# ---------------------------------------------------------------------------
+# Quadrature rules
+# ---------------------------------------------------------------------------
+def triangle_rule6():
+    """Symmetric 6-point degree-4 triangle rule (Dunavant 1985), in closed form.
+
+    Nodes (a, a, 1-2a) and (b, b, 1-2b) with
+      a = (8 - sqrt10 + sqrt(38 - 44 sqrt(2/5)))/18,  b = (8 - sqrt10 - sqrt(38 - 44 sqrt(2/5)))/18,
+    weights (620 +- sqrt(213125 - 53320 sqrt10))/3720 (normalised to sum 1)."""
+    s10 = math.sqrt(10.0)
+    r = math.sqrt(38.0 - 44.0 * math.sqrt(0.4))
+    a = (8.0 - s10 + r) / 18.0
+    b = (8.0 - s10 - r) / 18.0
+    q = math.sqrt(213125.0 - 53320.0 * s10)
+    wa = (620.0 + q) / 3720.0
+    wb = (620.0 - q) / 3720.0
+    bary = np.array(
+        [[1 - 2 * a, a, a], [a, 1 - 2 * a, a], [a, a, 1 - 2 * a],
+         [1 - 2 * b, b, b], [b, 1 - 2 * b, b], [b, b, 1 - 2 * b]], dtype=np.float64)
+    w = np.array([wa, wa, wa, wb, wb, wb], dtype=np.float64)
+    return bary, w
+
+
+def gauss_legendre01(n: int):
+    """n-point Gauss-Legendre rule on [0, 1] (numpy's leggauss, mapped)."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+# ---------------------------------------------------------------------------
+# RWG tables (Section IV: lowest-order div-conforming elements on flat triangles)
+# ---------------------------------------------------------------------------
+@dataclass
+class RWGMesh:
+    """Edges numbered in lexicographic order of their vertex pair (a < b).  Local edge i
+    of a triangle is the one opposite its local vertex i; the triangle is T+ of the edge
+    when the edge runs a -> b in the triangle's counter-clockwise order (sign +1), T-
+    otherwise (sign -1)."""
+
+    verts: np.ndarray
+    tris: np.ndarray
+    vnormals: np.ndarray
+    edges: np.ndarray = field(init=False)      # N x 2 (a < b)
+    edge_len: np.ndarray = field(init=False)   # N
+    edge_tris: np.ndarray = field(init=False)  # N x 2 (T+, T-)
+    tri_edge: np.ndarray = field(init=False)   # T x 3
+    tri_sign: np.ndarray = field(init=False)   # T x 3
+
+    def __post_init__(self):
+        self.verts = np.ascontiguousarray(self.verts, dtype=np.float64)
+        self.tris = np.ascontiguousarray(self.tris, dtype=np.int32)
+        T = self.tris.shape[0]
+        keys = {}
+        for t in range(T):
+            for i in range(3):
+                u, v = int(self.tris[t, (i + 1) % 3]), int(self.tris[t, (i + 2) % 3])
+                keys.setdefault((min(u, v), max(u, v)), []).append((t, i, +1.0 if u < v else -1.0))
+        order = sorted(keys)
+        N = len(order)
+        self.edges = np.array(order, dtype=np.int32).reshape(N, 2)
+        self.edge_len = np.linalg.norm(self.verts[self.edges[:, 1]] - self.verts[self.edges[:, 0]], axis=1)
+        self.edge_tris = np.zeros((N, 2), dtype=np.int32)
+        self.tri_edge = np.zeros((T, 3), dtype=np.int32)
+        self.tri_sign = np.zeros((T, 3), dtype=np.float64)
+        for m, key in enumerate(order):
+            occ = keys[key]
+            if len(occ) != 2 or occ[0][2] == occ[1][2]:
+                raise ValueError(f"edge {key} is not shared by two consistently oriented triangles")
+            for t, i, s in occ:
+                self.tri_edge[t, i] = m
+                self.tri_sign[t, i] = s
+                self.edge_tris[m, 0 if s > 0 else 1] = t
+        a = self.verts[self.tris[:, 0]]
+        self.tri_area = 0.5 * np.linalg.norm(np.cross(self.verts[self.tris[:, 1]] - a, self.verts[self.tris[:, 2]] - a), axis=1)
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.edges.shape[0])
+
+    @property
+    def nv(self) -> int:
+        return int(self.verts.shape[0])
+
+    @property
+    def nt(self) -> int:
+        return int(self.tris.shape[0])
+
+    def _args(self):
+        return (_p(self.verts), _p(self.tris), ctypes.c_int64(self.nt), _p(self.tri_edge), _p(self.tri_sign),
+                _p(self.edge_len))
+
+
+def from_synth(m) -> RWGMesh:
+    return RWGMesh(m.verts, m.tris, m.vnormals)
+
+
+# ---------------------------------------------------------------------------
+# EFIE matrix, right-hand side, far field (Sections II-B, II-C, IV-A)
+# ---------------------------------------------------------------------------
+def assemble_z(mesh: RWGMesh, k: float, n_ss: int = 5, threads: int | None = None) -> np.ndarray:
+    """Dense Galerkin matrix Z (N x N complex128) of the EFIO, Section IV-A (Z_L u_L = b_L)."""
+    qb, qw = triangle_rule6()
+    gx, gw = gauss_legendre01(n_ss)
+    N = mesh.n_edges
+    Z = np.zeros((N, N), dtype=np.complex128)
+    _load().orc_assemble_z(*mesh._args(), ctypes.c_int64(N), ctypes.c_double(k), _p(qb), _p(qw), ctypes.c_int(6),
+                           _p(gx), _p(gw), ctypes.c_int(n_ss), _p(Z), ctypes.c_int(threads or n_threads()))
+    return Z
+
+
+def z_entries(mesh: RWGMesh, k: float, rows, cols, n_ss: int = 5, threads: int | None = None) -> np.ndarray:
+    """Selected entries Z[rows[e], cols[e]] computed one by one (for large-N parity samples)."""
+    qb, qw = triangle_rule6()
+    gx, gw = gauss_legendre01(n_ss)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.zeros(rows.shape[0], dtype=np.complex128)
+    _load().orc_z_entries(*mesh._args(), _p(mesh.edge_tris), ctypes.c_double(k), _p(qb), _p(qw), ctypes.c_int(6),
+                          _p(gx), _p(gw), ctypes.c_int(n_ss), _p(rows), _p(cols), ctypes.c_int64(rows.shape[0]),
+                          _p(out), ctypes.c_int(threads or n_threads()))
+    return out
+
+
+def incidence(d, p):
+    """Pack plane waves E_inc = p exp(ik d.x) (Section V) as rows d(3), Re p(3), Im p(3)."""
+    d = np.atleast_2d(np.asarray(d, dtype=np.float64))
+    p = np.atleast_2d(np.asarray(p, dtype=np.complex128))
+    return np.ascontiguousarray(np.concatenate([d, p.real, p.imag], axis=1))
+
+
+def rhs_planewave(mesh: RWGMesh, k: float, d, p) -> np.ndarray:
+    """b_m = <gamma_D E_inc, f_m>_x = -int E_inc . f_m  (N x n_inc), Sections II-C and IV-A."""
+    inc = incidence(d, p)
+    qb, qw = triangle_rule6()
+    b = np.zeros((mesh.n_edges, inc.shape[0]), dtype=np.complex128)
+    _load().orc_rhs(*mesh._args(), ctypes.c_int64(mesh.n_edges), ctypes.c_double(k), _p(qb), _p(qw), ctypes.c_int(6),
+                    _p(inc), ctypes.c_int64(inc.shape[0]), _p(b))
+    return b
+
+
+def farfield_matrix(mesh: RWGMesh, k: float, xhat) -> np.ndarray:
+    """A (3 n_dir x N): F(xh_d)_c = sum_n A[3d + c, n] u_n, from E_sc = -E_k j and the
+    far-field expansion E_sc ~ exp(ik|x|)/(4 pi |x|) F (Section II-C)."""
+    xhat = np.ascontiguousarray(np.atleast_2d(xhat), dtype=np.float64)
+    qb, qw = triangle_rule6()
+    A = np.zeros((3 * xhat.shape[0], mesh.n_edges), dtype=np.complex128)
+    _load().orc_farfield_matrix(*mesh._args(), ctypes.c_int64(mesh.n_edges), ctypes.c_double(k), _p(qb), _p(qw),
+                                ctypes.c_int(6), _p(xhat), ctypes.c_int64(xhat.shape[0]), _p(A))
+    return A
+
+
+def solve(Z: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """u = Z^{-1} b (Section IV-A, eq. linear_system), LAPACK partial-pivot LU."""
+    return np.linalg.solve(Z, b)
+
+
+def rcs_db(F: np.ndarray) -> np.ndarray:
+    """RCS in dB of a far-field vector or component: sigma = 4 pi |E_sc|^2 r^2 = |F|^2/(4 pi)
+    with E_sc ~ exp(ik r)/(4 pi r) F and |p| = 1 (Section II-C, eq. RCS read with the
+    far-field normalisation of the expansion)."""
+    F = np.asarray(F)
+    mag2 = np.sum(np.abs(F) ** 2, axis=-1) if F.ndim >= 1 and F.shape[-1] == 3 else np.abs(F) ** 2
+    return 10.0 * np.log10(mag2 / (4.0 * np.pi))
+
+
+# ---------------------------------------------------------------------------
+# Shape derivative, covariance, combination technique (Sections III and IV)
+# ---------------------------------------------------------------------------
+def triangle_normals(mesh: RWGMesh) -> np.ndarray:
+    a = mesh.verts[mesh.tris[:, 0]]
+    n = np.cross(mesh.verts[mesh.tris[:, 1]] - a, mesh.verts[mesh.tris[:, 2]] - a)
+    return n / np.linalg.norm(n, axis=1, keepdims=True)
+
+
+def sd_rhs(mesh: RWGMesh, k: float, u: np.ndarray, vnormals=None, dense: bool = True):
+    """B (N x V): the shape-derivative right-hand side g = B xi of Section III (PEC),
+    for the normal perturbation v_n = sum_p xi_p psi_p (n_p . n_T), in weak form
+      B_mp = - sum_n u_n int psi_p nu_{p,T} [ik f_m.f_n + 1/(ik) div f_m div f_n]."""
+    vn = np.ascontiguousarray(mesh.vnormals if vnormals is None else vnormals, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.complex128).reshape(-1)
+    qb, qw = triangle_rule6()
+    vals = np.zeros((mesh.nt, 3, 3), dtype=np.complex128)
+    _load().orc_sd_rhs(*mesh._args(), ctypes.c_double(k), _p(qb), _p(qw), ctypes.c_int(6), _p(vn), _p(u), _p(vals))
+    rows = np.repeat(mesh.tri_edge[:, :, None], 3, axis=2).ravel()
+    cols = np.repeat(mesh.tris[:, None, :], 3, axis=1).ravel()
+    import scipy.sparse as sp
+    B = sp.coo_matrix((vals.ravel(), (rows, cols)), shape=(mesh.n_edges, mesh.nv)).tocsr()
+    return B.toarray() if dense else B
+
+
+def cov_kernel(x1: np.ndarray, x2: np.ndarray, kind: str, sigma: float, ell: float) -> np.ndarray:
+    """K_pq = sigma^2 rho(|x_p - x_q|): Gaussian rho = exp(-r^2/(2 l^2)) or Matern-3/2
+    rho = (1 + sqrt3 r/l) exp(-sqrt3 r/l), chordal distance: the second moment
+    M^2[v_n] of the random normal velocity (Section III) expanded at the mesh vertices."""
+    r = np.sqrt(np.maximum(((x1[:, None, :] - x2[None, :, :]) ** 2).sum(-1), 0.0))
+    if kind == "gauss":
+        return sigma**2 * np.exp(-(r**2) / (2 * ell**2))
+    if kind == "matern32":
+        s = math.sqrt(3.0) * r / ell
+        return sigma**2 * (1.0 + s) * np.exp(-s)
+    raise ValueError(kind)
+
+
+def covariance(Z1, B1, Z2, B2, K12, pseudo: bool = False) -> np.ndarray:
+    """Sigma_{l1,l2} solving (Z_l1 (x) conj Z_l2) Sigma = C_{l1,l2} (Sections IV-A/B,
+    eqs. linear_system2 and CTsubsystem), i.e. Z1 Sigma Z2^H = C with C = B1 K12 B2^H
+    (= E[g1 g2^H] for g = B xi).  pseudo=True gives Z1 S Z2^T = B1 K12 B2^T."""
+    C = B1 @ K12 @ (B2.T if pseudo else B2.conj().T)
+    Y = np.linalg.solve(Z1, C)                      # Z1^{-1} C
+    Z2x = Z2 if pseudo else Z2.conj()
+    return np.linalg.solve(Z2x, Y.T).T              # Y Z2^{-H}  (resp. Y Z2^{-T})
+
+
+def ct_index_sets(L0: int, L: int):
+    """Lambda_+ = {l1 + l2 = L + L0}, Lambda_- = {l1 + l2 = L + L0 - 1}, with
+    L0 <= l1, l2 <= L (Section IV-B)."""
+    lp = [(l1, L + L0 - l1) for l1 in range(L0, L + 1) if L0 <= L + L0 - l1 <= L]
+    lm = [(l1, L + L0 - 1 - l1) for l1 in range(L0, L + 1) if L0 <= L + L0 - 1 - l1 <= L]
+    return lp, lm
+
+
+def ct_hermitian_blocks(L0: int, L: int):
+    """Blocks with l1 >= l2 and their signs (+1 on Lambda_+, -1 on Lambda_-): the
+    Hermitian reduction Sigma_{l2,l1} = Sigma_{l1,l2}^H of Section IV-B."""
+    lp, lm = ct_index_sets(L0, L)
+    return [(b, +1) for b in lp if b[0] >= b[1]] + [(b, -1) for b in lm if b[0] >= b[1]]
+
+
+def ct_dofs(N, L0: int, L: int, hermitian: bool = False):
+    """N_hat_L = sum over Lambda of N_l1 N_l2 and N_hat_L^max (eq. efficiency, Section IV-B).
+    N maps level -> number of dofs."""
+    lp, lm = ct_index_sets(L0, L)
+    blocks = lp + lm
+    if hermitian:
+        blocks = [b for b in blocks if b[0] >= b[1]]
+    sizes = [N[a] * N[b] for a, b in blocks]
+    return sum(sizes), max(sizes)
+
+
+@dataclass
+class Level:
+    mesh: RWGMesh
+    Z: np.ndarray
+    u: np.ndarray
+    A: np.ndarray
+    B: np.ndarray
+
+
+def nominal_level(mesh: RWGMesh, k: float, d, p, xhat, n_ss: int = 5) -> Level:
+    """Assemble, solve and map one level: Z_l, u_l = Z_l^{-1} b_l, A_l, B_l(u_l)."""
+    Z = assemble_z(mesh, k, n_ss)
+    b = rhs_planewave(mesh, k, d, p)[:, 0]
+    u = solve(Z, b)
+    A = farfield_matrix(mesh, k, xhat)
+    B = sd_rhs(mesh, k, u)
+    return Level(mesh, Z, u, A, B)
+
+
+def ct_farfield_covariance(levels: dict, L0: int, L: int, kernel: str, sigma: float, ell: float,
+                           pseudo: bool = False) -> np.ndarray:
+    """Far-field covariance of the combination technique (Section IV-B):
+      Cov_hat = sum_{Lambda_+} A_l1 Sigma_{l1,l2} A_l2^H - sum_{Lambda_-} (same),
+    computed for l1 >= l2 and mirrored (M + M^H) when l1 != l2.  pseudo=True gives the
+    pseudo-covariance sum A_l1 S_{l1,l2} A_l2^T (mirrored with the transpose)."""
+    out = None
+    for (l1, l2), sgn in ct_hermitian_blocks(L0, L):
+        a, b = levels[l1], levels[l2]
+        K = cov_kernel(a.mesh.verts, b.mesh.verts, kernel, sigma, ell)
+        S = covariance(a.Z, a.B, b.Z, b.B, K, pseudo)
+        M = a.A @ S @ (b.A.T if pseudo else b.A.conj().T)
+        if l1 != l2:
+            M = M + (M.T if pseudo else M.conj().T)
+        out = sgn * M if out is None else out + sgn * M
+    return out
+
+
+def rcs_variance_db(F: np.ndarray, cov: np.ndarray, pcov: np.ndarray) -> np.ndarray:
+    """Delta-method variance of RCS_dB = 10 log10(|F|^2/(4 pi)) at each direction:
+    Var = (20/ln 10)^2 Var[Re(conj F . F')]/|F|^4 with Var[Re z] = (E|z|^2 + Re E[z^2])/2,
+    E|z|^2 = F^H-weighted covariance, E[z^2] from the pseudo-covariance.
+    F: n_dir x 3; cov, pcov: (3 n_dir) x (3 n_dir)."""
+    n = F.shape[0]
+    out = np.zeros(n)
+    for d in range(n):
+        f = F[d]
+        C = cov[3 * d:3 * d + 3, 3 * d:3 * d + 3]
+        P = pcov[3 * d:3 * d + 3, 3 * d:3 * d + 3]
+        ez2 = np.conj(f) @ C @ f             # E[z conj z], z = conj(f) . F'
+        ezz = np.conj(f) @ P @ np.conj(f)    # E[z z]
+        var_re = 0.5 * (ez2.real + ezz.real)
+        out[d] = (20.0 / math.log(10.0)) ** 2 * var_re / np.sum(np.abs(f) ** 2) ** 2
+    return out
