@@ -1,0 +1,215 @@
+/*
+ * fosb.h -- C ABI of the GB300 (sm_103a) FOSB / EFIE library.
+ *
+ * The library computes, on one GPU, the data-parallel hot path of the first-order
+ * sparse boundary element method (FOSB) for a perfectly conducting scatterer
+ * (Escapil-Inchauspe & Jerez-Hanckes, "Shape UQ for EM wave scattering via FOSB
+ * approximation", arXiv:2308.01457):
+ *
+ *   - Galerkin assembly of the EFIE  <T_k j, phi>_x = <gamma_D E_inc, phi>_x
+ *     with lowest-order RWG elements (Section II-B eq. boundary_operators, Section
+ *     II-C eq. pec, Section IV-A), Z_L u_L = b_L (eq. linear_system);
+ *   - LU factorisation and solves (FP64, or FP32 factors with FP64 iterative
+ *     refinement) giving the nominal current u_L;
+ *   - the first-order shape-derivative covariance: the tensor system
+ *     (Z_l1 (x) conj Z_l2) Sigma_{l1,l2} = C_{l1,l2} (eq. linear_system2, eq.
+ *     CTsubsystem) with C = E[g g^H] built from the PEC shape-derivative right-hand
+ *     side g of Section III (eq. secondPEC);
+ *   - far-field and RCS moments (Section II-C, the far-field expansion and eq. RCS),
+ *     combined over the combination-technique index sets Lambda_+/- (Section IV-B).
+ *
+ * Conventions (every call):
+ *   - Complex arrays are interleaved (re, im): complex128 = 2 doubles, complex64 =
+ *     2 floats.  Matrices are ROW-MAJOR with an explicit leading dimension (in
+ *     elements).
+ *   - Pointers documented "device" are caller-owned device memory (the library never
+ *     frees them); "host" pointers are read during the call only.  Handles
+ *     (fosb_mesh, fosb_lu) own library-allocated device memory released by their
+ *     destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device work is enqueued on it; calls return after enqueueing unless stated.
+ *   - Argument and mesh errors are detected on the host and returned before any
+ *     work is enqueued.  CUDA launch errors return FOSB_ERR_CUDA.  A failed call
+ *     leaves its outputs unspecified, except FOSB_ERR_NOT_CONVERGED, where the best
+ *     iterate is written.  fosb_last_error() gives a thread-local message.
+ *
+ * RWG numbering (shared contract with any checker): edges are the unordered vertex
+ * pairs (a < b) in lexicographic order; local edge i of a triangle is opposite its
+ * local vertex i; the basis function of edge m is
+ *     f_m(x) = +l_m/(2 A_+) (x - p_+) on T_+,   f_m(x) = -l_m/(2 A_-) (x - p_-) on T_-,
+ * where T_+ is the triangle whose counter-clockwise order runs a -> b, and p_+/- are
+ * the opposite vertices (Section IV: div-conforming lowest-order elements).
+ */
+#ifndef FOSB_H
+#define FOSB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fosb_status;
+enum {
+  FOSB_OK = 0,
+  FOSB_ERR_INVALID_ARG = 1,   /* bad pointer, size, option or leading dimension */
+  FOSB_ERR_MESH = 2,          /* non-manifold, degenerate or inconsistently oriented mesh */
+  FOSB_ERR_SINGULAR = 3,      /* exactly zero pivot in the LU factorisation */
+  FOSB_ERR_NOT_CONVERGED = 4, /* iterative refinement stalled; best iterate written */
+  FOSB_ERR_OOM = 5,           /* device allocation failed */
+  FOSB_ERR_CUDA = 6,          /* CUDA runtime / launch error */
+  FOSB_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up (status word set) */
+};
+
+/* Arithmetic of a call.
+ *   FOSB_FP64  : all arithmetic in FP64; Z and solutions complex128.
+ *   FOSB_MIXED : FP64-accurate Z (complex128), complex64 LU factors, FP64 residuals
+ *                and iterative refinement to FP64 accuracy; outputs complex128.
+ *   FOSB_FP32  : complex64 Z, LU and solutions, no refinement (about 1e-4 relative). */
+typedef enum { FOSB_FP64 = 0, FOSB_MIXED = 1, FOSB_FP32 = 2 } fosb_precision;
+
+/* Regular-pair assembly arithmetic (singular pairs are always FP64):
+ *   FOSB_ASM_FP64  : FP64 everywhere;
+ *   FOSB_ASM_FF    : float-float (unevaluated sums of two floats, ~48-bit significand)
+ *                    on the FP32 pipe -- FP64-class accuracy at FP32 throughput;
+ *   FOSB_ASM_FP32  : plain FP32 (the 1e-4 path). */
+typedef enum { FOSB_ASM_FP64 = 0, FOSB_ASM_FF = 1, FOSB_ASM_FP32 = 2 } fosb_asm_arith;
+
+typedef struct {
+  int n_ss;        /* Gauss-Legendre points per coordinate of the Sauter-Schwab 4-cube (1..12), default 5 */
+  int arith;       /* fosb_asm_arith for the regular pairs, default FOSB_ASM_FP64 */
+} fosb_quad_opts;
+
+typedef struct {
+  int max_iters;     /* iterative-refinement steps (default 10) */
+  double tol;        /* stop when ||b - Z x||_inf / (||Z||_inf ||x||_inf + ||b||_inf) <= tol (default 64 * 2^-52) */
+} fosb_refine_opts;
+
+typedef struct {
+  int iters;             /* refinement steps taken (0 for FOSB_FP64 / FOSB_FP32) */
+  double backward_error; /* final normwise relative backward error (max over right-hand sides) */
+} fosb_solve_stats;
+
+typedef enum { FOSB_COV_GAUSS = 0, FOSB_COV_MATERN32 = 1 } fosb_cov_kind;
+typedef struct {
+  int kind;      /* fosb_cov_kind: sigma^2 exp(-r^2/(2 l^2)) or sigma^2 (1 + sqrt3 r/l) exp(-sqrt3 r/l) */
+  double sigma;  /* pointwise standard deviation of the normal velocity v_n */
+  double ell;    /* correlation length l (chordal distance r between mesh vertices) */
+} fosb_cov_kernel;
+
+typedef struct fosb_mesh_s* fosb_mesh;
+typedef struct fosb_lu_s* fosb_lu;
+
+/* Thread-local description of the last error (library-owned, valid until the next call). */
+const char* fosb_last_error(void);
+
+/* Library version string. */
+const char* fosb_version(void);
+
+/* ---- A1: mesh tables ------------------------------------------------------------
+ * Builds the RWG tables of a closed, orientable, manifold triangulation (Section IV,
+ * meshes Gamma_{h_l} of planar triangles) and uploads them to the current device.
+ *   verts    : host, nv x 3 float64 vertex coordinates
+ *   tris     : host, nt x 3 int32, counter-clockwise seen from outside
+ *   vnormals : host, nv x 3 unit outward vertex normals n_p used for the normal
+ *              perturbation v_n (Section III); NULL -> area-weighted normals
+ *   out      : receives the handle (library-owned; free with fosb_mesh_destroy)
+ * Errors: FOSB_ERR_INVALID_ARG (NULL/size), FOSB_ERR_MESH (index out of range,
+ * degenerate triangle, edge not shared by exactly two oppositely oriented triangles,
+ * non-finite coordinate), FOSB_ERR_OOM. */
+fosb_status fosb_mesh_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                             const double* vnormals, fosb_mesh* out);
+
+/* Sizes of a mesh: vertices, triangles, RWG edges (= unknowns N), touching triangle
+ * pairs (unordered, including identical pairs).  Any output pointer may be NULL. */
+fosb_status fosb_mesh_info(fosb_mesh mesh, int64_t* nv, int64_t* nt, int64_t* n_edges, int64_t* n_touching);
+
+/* Host copy of the edge table: edges (N x 2 int32, a < b) and edge_tris (N x 2 int32,
+ * T_+ then T_-).  Either pointer may be NULL. */
+fosb_status fosb_mesh_edges(fosb_mesh mesh, int32_t* edges, int32_t* edge_tris);
+
+fosb_status fosb_mesh_destroy(fosb_mesh mesh);
+
+/* ---- A2-A4: EFIE assembly and plane-wave right-hand sides --------------------------
+ * Z[m, n] = <T_k f_n, f_m>_x = -[ ik int int G f_m . f_n + 1/(ik) int int G div f_m div f_n ],
+ * G = exp(ik|x-y|)/(4 pi |x-y|) (Section II-B), and
+ * b[m, s] = <gamma_D E_inc_s, f_m>_x = -int E_inc_s . f_m, E_inc_s = p_s exp(ik d_s . x)
+ * (Section V, eq. incidentNumexp).  Regular triangle pairs use the 6-point degree-4
+ * triangle rule in x and y; pairs sharing a vertex, an edge, or identical use the
+ * Sauter-Schwab regularised 4-cube rule with opts->n_ss Gauss points per coordinate.
+ *   k       : wavenumber > 0
+ *   opts    : quadrature options (NULL -> defaults)
+ *   prec    : FOSB_FP64 / FOSB_MIXED write complex128 Z; FOSB_FP32 writes complex64 Z
+ *   Z       : device, N x N, row-major, leading dimension ldz >= N; overwritten
+ *   inc     : host, n_inc x 9 float64: d (3, unit), Re p (3), Im p (3); may be NULL if n_inc = 0
+ *   b       : device, N x n_inc (leading dimension ldb >= n_inc), same complex type as Z; may be NULL
+ * Errors: FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_assemble_efie(fosb_mesh mesh, double k, const fosb_quad_opts* opts, int prec, void* Z, int64_t ldz,
+                               const double* inc, int64_t n_inc, void* b, int64_t ldb, void* stream);
+
+/* ---- A5: LU factorisation -----------------------------------------------------------
+ * P Z = L U with partial pivoting (largest |Re| + |Im|, ties to the lowest row).
+ *   Z    : device, n x n row-major (complex128 for FP64/MIXED, complex64 for FP32);
+ *          read, not modified.  For FOSB_MIXED the handle keeps a NON-owning reference
+ *          to Z for the FP64 residuals: Z must stay alive and unchanged until
+ *          fosb_lu_destroy.
+ *   out  : receives a handle owning the factors and pivots (device memory).
+ * Synchronises `stream` at the end (the pivot search reports FOSB_ERR_SINGULAR). */
+fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu* out, void* stream);
+
+/* ---- A6: solves with iterative refinement -----------------------------------------
+ * X = Z^{-1} B (op = 'N').  Z is complex symmetric for the EFIE, so Z^{-T} = Z^{-1}.
+ *   B, X : device, n x nrhs row-major (ldb, ldx >= nrhs), complex128 for FP64/MIXED,
+ *          complex64 for FP32.  X may alias B.
+ *   ropt : refinement options (MIXED only; NULL -> defaults); stats may be NULL.
+ * MIXED: x0 from the complex64 factors, then r = b - Z x in FP64, x += LU^{-1} r until
+ * the backward error is below tol; synchronises `stream` once per step.
+ * Errors: FOSB_ERR_NOT_CONVERGED (best iterate written). */
+fosb_status fosb_solve(fosb_lu lu, char op, const void* B, int64_t nrhs, int64_t ldb, void* X, int64_t ldx,
+                       const fosb_refine_opts* ropt, fosb_solve_stats* stats, void* stream);
+
+fosb_status fosb_lu_info(fosb_lu lu, int64_t* n, int* prec, double* znorm_inf);
+fosb_status fosb_lu_destroy(fosb_lu lu);
+
+/* ---- A7-A9: shape-derivative covariance of one combination-technique block --------
+ * Sigma solves (Z_1 (x) conj Z_2) Sigma = C (eq. CTsubsystem), i.e. Z_1 Sigma Z_2^H = C,
+ * with C = B_1 K_12 B_2^H = E[g_1 g_2^H]:
+ *   B_l (N_l x V_l): g = B xi is the Galerkin right-hand side <g, f_m>_x of the PEC
+ *   shape-derivative problem T_k dj' = grad_G[v_n E_n] x n - ik v_n gamma_T H
+ *   (Section III) for v_n = sum_p xi_p psi_p (n_p . n_T), evaluated at the nominal
+ *   current u_l of that level:  B_mp = -sum_n u_n int psi_p (n_p . n_T) [ik f_m . f_n
+ *   + 1/(ik) div f_m div f_n];
+ *   K_12[p, q] = kernel(|x_p^(1) - x_q^(2)|) between the vertices of the two meshes.
+ * pseudo = 1 gives the pseudo-covariance Z_1 S Z_2^T = B_1 K_12 B_2^T instead.
+ *   m1, m2   : meshes of levels l1 and l2 (may be the same handle)
+ *   lu1, lu2 : factorisations of Z_l1, Z_l2 (same precision; MIXED refines both solves)
+ *   u1, u2   : device, nominal currents (N_l, complex128 or complex64 per precision)
+ *   Sigma    : device, N_1 x N_2 row-major (leading dimension lds), overwritten
+ * The product is evaluated as Sigma = (Z_1^{-1} B_1 K_12)(Z_2^{-1} B_2)^H when V_2 <= V_1
+ * (and symmetrically otherwise): the same Sigma with min(V_1, V_2) right-hand sides.
+ * Synchronises `stream` (refinement).  Errors: FOSB_ERR_NOT_CONVERGED. */
+fosb_status fosb_covariance(fosb_mesh m1, fosb_lu lu1, const void* u1, fosb_mesh m2, fosb_lu lu2, const void* u2,
+                            double k, const fosb_cov_kernel* kernel, int pseudo, void* Sigma, int64_t lds,
+                            const fosb_refine_opts* ropt, void* stream);
+
+/* ---- A10-A11: far-field moments --------------------------------------------------
+ * Far-field matrix A_l (3 n_dir x N_l): F(xh_d)_c = sum_n A[3d + c, n] u_n, from
+ * E_sc = -E_k j and E_sc ~ exp(ik|x|)/(4 pi |x|) F (Section II-C):
+ *     A[3d + c, n] = -ik [(I - xh xh^T) int f_n(y) exp(-ik xh . y) dy]_c  (6-point rule).
+ * Mean mode (m2 == NULL): out (3 n_dir x ncols, leading dimension ldo) = weight * A_1 X,
+ *   X device N_1 x ncols (ldx).
+ * Covariance mode (m2 != NULL): out (3 n_dir x 3 n_dir, ldo) = weight * M,
+ *   M = A_1 X A_2^H (pseudo = 0) or A_1 X A_2^T (pseudo = 1), X = Sigma (N_1 x N_2, ldx);
+ *   hermitian_mirror = 1 adds M^H (resp. M^T): the Hermitian reduction of Section IV-B
+ *   for an off-diagonal block (l1 != l2).
+ * accumulate = 1 adds into out instead of overwriting (CT signed sum: weight = +1 on
+ * Lambda_+, -1 on Lambda_-).  dirs: host n_dir x 3 unit vectors.  Complex128 (prec
+ * FP64/MIXED) or complex64 (FP32) throughout. */
+fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const double* dirs, int64_t n_dir,
+                                  const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
+                                  int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOSB_H */

@@ -1,0 +1,220 @@
+"""Python binding of the GB300 FOSB/EFIE library (``libfosb.so``, C ABI in include/fosb.h).
+
+Argument marshalling only: every step runs in the CUDA kernels behind the C ABI.
+Device buffers are torch CUDA tensors (used for memory and streams); host inputs are
+numpy arrays.  If the shared library is missing or cannot be loaded, every call
+raises -- there is no CPU fallback.
+
+The call names mirror the C ABI (fosb_mesh_create -> mesh_create, ...).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FOSB_OK, FOSB_ERR_INVALID_ARG, FOSB_ERR_MESH, FOSB_ERR_SINGULAR, FOSB_ERR_NOT_CONVERGED, FOSB_ERR_OOM, \
+    FOSB_ERR_CUDA, FOSB_ERR_TIMEOUT = range(8)
+FP64, MIXED, FP32 = 0, 1, 2
+ASM_FP64, ASM_FF, ASM_FP32 = 0, 1, 2
+COV_GAUSS, COV_MATERN32 = 0, 1
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "MESH", 3: "SINGULAR", 4: "NOT_CONVERGED", 5: "OOM", 6: "CUDA", 7: "TIMEOUT"}
+
+_lib = None
+
+
+class FosbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"FOSB_ERR_{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class QuadOpts(ctypes.Structure):
+    _fields_ = [("n_ss", ctypes.c_int), ("arith", ctypes.c_int)]
+
+
+class RefineOpts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
+
+
+class CovKernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("ell", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libfosb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libfosb.so not built ({path}); run __graft_entry__.build() or "
+                               "python -m paper_2308_01457_gb300.build")
+        L = ctypes.CDLL(path)
+        L.fosb_last_error.restype = ctypes.c_char_p
+        L.fosb_version.restype = ctypes.c_char_p
+        for name in ("fosb_mesh_create", "fosb_mesh_info", "fosb_mesh_edges", "fosb_mesh_destroy",
+                     "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
+                     "fosb_covariance", "fosb_farfield_moments"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != FOSB_OK:
+        raise FosbError(status, lib().fosb_last_error().decode())
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ld(t) -> int:
+    """Leading dimension (row stride, in elements) of a row-major 2-D tensor."""
+    if t.dim() == 1:
+        return 1
+    if t.stride(1) != 1:
+        raise ValueError("tensor rows must be contiguous")
+    return t.stride(0)
+
+
+def _prec_of(t) -> int:
+    import torch
+
+    return FP32 if t.dtype == torch.complex64 else FP64
+
+
+class Mesh:
+    """Handle of fosb_mesh_create (RWG tables on the device)."""
+
+    def __init__(self, verts, tris, vnormals=None):
+        v = _np(verts, np.float64)
+        t = _np(tris, np.int32)
+        vn = None if vnormals is None else _np(vnormals, np.float64)
+        h = ctypes.c_void_p()
+        _check(lib().fosb_mesh_create(v.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(v.shape[0]),
+                                      t.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(t.shape[0]),
+                                      None if vn is None else vn.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self.handle = h
+        nv, nt, ne, ntouch = (ctypes.c_int64() for _ in range(4))
+        _check(lib().fosb_mesh_info(h, ctypes.byref(nv), ctypes.byref(nt), ctypes.byref(ne), ctypes.byref(ntouch)))
+        self.nv, self.nt, self.n_edges, self.n_touching = nv.value, nt.value, ne.value, ntouch.value
+
+    def edges(self):
+        e = np.zeros((self.n_edges, 2), np.int32)
+        et = np.zeros((self.n_edges, 2), np.int32)
+        _check(lib().fosb_mesh_edges(self.handle, e.ctypes.data_as(ctypes.c_void_p), et.ctypes.data_as(ctypes.c_void_p)))
+        return e, et
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fosb_mesh_destroy(self.handle)
+            self.handle = None
+
+
+def mesh_create(verts, tris, vnormals=None) -> Mesh:
+    return Mesh(verts, tris, vnormals)
+
+
+def incidence(d, p) -> np.ndarray:
+    """Plane waves p exp(ik d.x) packed as rows d(3), Re p(3), Im p(3)."""
+    d = np.atleast_2d(np.asarray(d, np.float64))
+    p = np.atleast_2d(np.asarray(p, np.complex128))
+    return np.ascontiguousarray(np.concatenate([d, p.real, p.imag], axis=1))
+
+
+def assemble_efie(mesh: Mesh, k: float, Z, inc=None, b=None, n_ss: int = 5, arith: int = ASM_FP64,
+                  prec: int | None = None, stream=None):
+    """fosb_assemble_efie: writes Z (N x N) and, if inc is given, b (N x n_inc)."""
+    prec = _prec_of(Z) if prec is None else prec
+    opts = QuadOpts(n_ss, arith)
+    inc_a = None if inc is None else _np(inc, np.float64).reshape(-1, 9)
+    n_inc = 0 if inc_a is None else inc_a.shape[0]
+    _check(lib().fosb_assemble_efie(mesh.handle, ctypes.c_double(k), ctypes.byref(opts), ctypes.c_int(prec), _ptr(Z),
+                                    ctypes.c_int64(_ld(Z)),
+                                    None if inc_a is None else inc_a.ctypes.data_as(ctypes.c_void_p),
+                                    ctypes.c_int64(n_inc), None if b is None else _ptr(b),
+                                    ctypes.c_int64(_ld(b) if b is not None else 0), _stream(stream)))
+
+
+class LU:
+    """Handle of fosb_factor (owns the factors; MIXED keeps a reference to Z)."""
+
+    def __init__(self, handle, n, prec, zref):
+        self.handle, self.n, self.prec, self._zref = handle, n, prec, zref
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fosb_lu_destroy(self.handle)
+            self.handle = None
+
+
+def factor(Z, prec: int | None = None, stream=None) -> LU:
+    prec = _prec_of(Z) if prec is None else prec
+    h = ctypes.c_void_p()
+    _check(lib().fosb_factor(_ptr(Z), ctypes.c_int64(Z.shape[0]), ctypes.c_int64(_ld(Z)), ctypes.c_int(prec),
+                             ctypes.byref(h), _stream(stream)))
+    return LU(h, Z.shape[0], prec, Z)
+
+
+def solve(lu: LU, B, X=None, max_iters: int = 10, tol: float = 64 * 2.0**-52, stream=None):
+    """fosb_solve: X = Z^{-1} B (in place when X is None).  Returns (X, iters, backward_error)."""
+    X = B if X is None else X
+    nrhs = 1 if B.dim() == 1 else B.shape[1]
+    st = SolveStats()
+    ro = RefineOpts(max_iters, tol)
+    _check(lib().fosb_solve(lu.handle, ctypes.c_char(b"N"), _ptr(B), ctypes.c_int64(nrhs),
+                            ctypes.c_int64(1 if B.dim() == 1 else _ld(B)), _ptr(X), ctypes.c_int64(1 if X.dim() == 1 else _ld(X)),
+                            ctypes.byref(ro), ctypes.byref(st), _stream(stream)))
+    return X, st.iters, st.backward_error
+
+
+def covariance(m1: Mesh, lu1: LU, u1, m2: Mesh, lu2: LU, u2, k: float, Sigma, kind: int = COV_GAUSS,
+               sigma: float = 1.0, ell: float = 1.0, pseudo: bool = False, max_iters: int = 10,
+               tol: float = 64 * 2.0**-52, stream=None):
+    """fosb_covariance: Sigma (N1 x N2) with Z1 Sigma Z2^H = B1 K12 B2^H (or the pseudo form)."""
+    ker = CovKernel(kind, sigma, ell)
+    ro = RefineOpts(max_iters, tol)
+    _check(lib().fosb_covariance(m1.handle, lu1.handle, _ptr(u1), m2.handle, lu2.handle, _ptr(u2), ctypes.c_double(k),
+                                 ctypes.byref(ker), ctypes.c_int(int(pseudo)), _ptr(Sigma), ctypes.c_int64(_ld(Sigma)),
+                                 ctypes.byref(ro), _stream(stream)))
+    return Sigma
+
+
+def farfield_moments(m1: Mesh, k: float, dirs, X, out, m2: Mesh | None = None, weight: float = 1.0,
+                     mirror: bool = False, pseudo: bool = False, accumulate: bool = False, prec: int | None = None,
+                     stream=None):
+    """fosb_farfield_moments.  Mean mode (m2 None): out = w A1 X.  Covariance mode:
+    out = w A1 X A2^H (+ its ^H if mirror; ^T variants if pseudo)."""
+    d = _np(dirs, np.float64).reshape(-1, 3)
+    prec = _prec_of(X) if prec is None else prec
+    ncols = 1 if X.dim() == 1 else X.shape[1]
+    _check(lib().fosb_farfield_moments(m1.handle, None if m2 is None else m2.handle, ctypes.c_double(k),
+                                       d.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(d.shape[0]), _ptr(X),
+                                       ctypes.c_int64(1 if X.dim() == 1 else _ld(X)), ctypes.c_int64(ncols),
+                                       ctypes.c_double(weight), ctypes.c_int(int(mirror)), ctypes.c_int(int(pseudo)),
+                                       ctypes.c_int(prec), _ptr(out), ctypes.c_int64(1 if out.dim() == 1 else _ld(out)),
+                                       ctypes.c_int(int(accumulate)), _stream(stream)))
+    return out

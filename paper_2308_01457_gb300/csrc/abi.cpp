@@ -1,0 +1,354 @@
+// extern "C" entry points: argument checks, scratch management and the host loops
+// (iterative refinement) around the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fosb_internal.h"
+
+using namespace fosb;
+
+namespace {
+
+// Stream-ordered scratch buffer released at scope exit.
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, std::max<size_t>(bytes, 16), s); }
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+int g_rules_nss[64];  // per device: the n_ss whose rules are in constant memory (0 = none)
+
+fosb_status ensure_rules(int nss) {
+  int dev = 0;
+  FOSB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(FOSB_ERR_INVALID_ARG, "device index out of range");
+  if (g_rules_nss[dev] != nss) {
+    upload_rules(make_rules(nss));
+    FOSB_CUDA(cudaDeviceSynchronize());
+    g_rules_nss[dev] = nss;
+  }
+  return FOSB_OK;
+}
+
+bool is_c64(int prec) { return prec == FOSB_FP32; }
+
+fosb_status check_prec(int prec) {
+  if (prec != FOSB_FP64 && prec != FOSB_MIXED && prec != FOSB_FP32)
+    return fail(FOSB_ERR_INVALID_ARG, "unknown precision");
+  return FOSB_OK;
+}
+
+fosb_status col_norms(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_buf, std::vector<double>& out,
+                      cudaStream_t s) {
+  FOSB_CUDA(absmax_c128(A, rows, cols, lda, d_buf, s));
+  out.resize(cols);
+  FOSB_CUDA(cudaMemcpyAsync(out.data(), d_buf, sizeof(double) * cols, cudaMemcpyDeviceToHost, s));
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  return FOSB_OK;
+}
+
+// X = Z^{-1} B through the handle (see fosb_solve).
+fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb, void* X, int64_t ldx,
+                           const fosb_refine_opts* ropt, fosb_solve_stats* stats, cudaStream_t s) {
+  const int64_t n = lu->n;
+  if (stats) {
+    stats->iters = 0;
+    stats->backward_error = 0.0;
+  }
+  if (nrhs == 0 || n == 0) return FOSB_OK;
+  if (lu->prec == FOSB_FP64) {
+    if (X != B) FOSB_CUDA(copy_matrix(B, n, nrhs, ldb, X, ldx, 16, s));
+    FOSB_CUDA(getrs<double>(lu->lu, n, n, lu->ipiv, X, nrhs, ldx, s));
+    return FOSB_OK;
+  }
+  if (lu->prec == FOSB_FP32) {
+    if (X != B) FOSB_CUDA(copy_matrix(B, n, nrhs, ldb, X, ldx, 8, s));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, X, nrhs, ldx, s));
+    return FOSB_OK;
+  }
+  // MIXED: complex64 factors, FP64 residuals.
+  const int max_iters = ropt ? ropt->max_iters : 10;
+  const double tol = ropt ? ropt->tol : 64.0 * std::ldexp(1.0, -52);
+  Scratch r(s), d(s), bkeep(s), nb(s);
+  FOSB_CUDA(r.alloc(sizeof(double) * 2 * n * nrhs));
+  FOSB_CUDA(d.alloc(sizeof(float) * 2 * n * nrhs));
+  FOSB_CUDA(nb.alloc(sizeof(double) * nrhs));
+  const void* Bsrc = B;
+  int64_t ldbs = ldb;
+  if (X == B) {  // keep the right-hand side: X is overwritten
+    FOSB_CUDA(bkeep.alloc(sizeof(double) * 2 * n * nrhs));
+    FOSB_CUDA(copy_matrix(B, n, nrhs, ldb, bkeep.p, nrhs, 16, s));
+    Bsrc = bkeep.p;
+    ldbs = nrhs;
+  }
+  std::vector<double> bn, xn, rn;
+  FOSB_TRY(col_norms(Bsrc, n, nrhs, ldbs, nb.as<double>(), bn, s));
+  // x0
+  FOSB_CUDA(convert_c128_to_c64(Bsrc, n, nrhs, ldbs, d.p, nrhs, s));
+  FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s));
+  FOSB_CUDA(convert_c64_to_c128(d.p, n, nrhs, nrhs, X, ldx, s));
+  double prev = INFINITY, prev2 = INFINITY, berr = INFINITY;
+  int it = 0;
+  for (;;) {
+    FOSB_CUDA(copy_matrix(Bsrc, n, nrhs, ldbs, r.p, nrhs, 16, s));
+    FOSB_CUDA(gemm<double>(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s));
+    FOSB_TRY(col_norms(r.p, n, nrhs, nrhs, nb.as<double>(), rn, s));
+    FOSB_TRY(col_norms(X, n, nrhs, ldx, nb.as<double>(), xn, s));
+    berr = 0.0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      double den = lu->znorm_inf * xn[c] + bn[c];
+      berr = std::max(berr, den > 0 ? rn[c] / den : 0.0);
+    }
+    if (berr <= tol || it >= max_iters) break;
+    if (berr >= prev && prev >= prev2) break;  // no decrease over two steps
+    prev2 = prev;
+    prev = berr;
+    FOSB_CUDA(convert_c128_to_c64(r.p, n, nrhs, nrhs, d.p, nrhs, s));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s));
+    FOSB_CUDA(axpy_c64_into_c128(d.p, n, nrhs, nrhs, X, ldx, s));
+    ++it;
+  }
+  if (stats) {
+    stats->iters = it;
+    stats->backward_error = berr;
+  }
+  if (!(berr <= tol) && !(berr <= 1e-13)) {
+    return fail(FOSB_ERR_NOT_CONVERGED, "fosb_solve: refinement stalled at backward error " + std::to_string(berr));
+  }
+  return FOSB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fosb_status fosb_assemble_efie(fosb_mesh mesh, double k, const fosb_quad_opts* opts, int prec, void* Z, int64_t ldz,
+                               const double* inc, int64_t n_inc, void* b, int64_t ldb, void* stream) {
+  if (!mesh || !Z) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: NULL mesh or Z");
+  FOSB_TRY(check_prec(prec));
+  const int64_t N = mesh->d.ne;
+  if (!(k > 0.0) || !std::isfinite(k)) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: k must be > 0");
+  if (ldz < N) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: ldz < N");
+  if (n_inc < 0 || (n_inc > 0 && (!inc || !b || ldb < n_inc)))
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: bad incidence arguments");
+  int nss = opts && opts->n_ss > 0 ? opts->n_ss : 5;
+  int arith = opts ? opts->arith : FOSB_ASM_FP64;
+  if (nss > 12) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: n_ss must be in 1..12");
+  if (arith < 0 || arith > 2) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: unknown arith");
+  if (is_c64(prec)) arith = FOSB_ASM_FP32;
+  else if (arith == FOSB_ASM_FP32)
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: FP32 regular pairs need prec = FOSB_FP32");
+  for (int64_t s = 0; s < n_inc; ++s)
+    for (int c = 0; c < 9; ++c)
+      if (!std::isfinite(inc[9 * s + c])) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: non-finite incidence");
+  FOSB_TRY(ensure_rules(nss));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t elem = is_c64(prec) ? 8 : 16;
+  FOSB_CUDA(cudaMemset2DAsync(Z, ldz * elem, 0, N * elem, N, s));
+  FOSB_CUDA(launch_assemble_regular(mesh->d, k, arith, Z, ldz, s));
+  FOSB_CUDA(launch_assemble_singular(mesh->d, k, nss, is_c64(prec), Z, ldz, s));
+  if (n_inc > 0) {
+    Scratch dinc(s);
+    FOSB_CUDA(dinc.alloc(sizeof(double) * 9 * n_inc));
+    FOSB_CUDA(cudaMemcpyAsync(dinc.p, inc, sizeof(double) * 9 * n_inc, cudaMemcpyHostToDevice, s));
+    FOSB_CUDA(cudaMemset2DAsync(b, ldb * elem, 0, n_inc * elem, N, s));
+    FOSB_CUDA(launch_rhs(mesh->d, k, dinc.as<double>(), n_inc, is_c64(prec), b, ldb, s));
+    FOSB_CUDA(cudaStreamSynchronize(s));  // the host incidence copy must finish before scratch reuse
+  }
+  return FOSB_OK;
+}
+
+fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu* out, void* stream) {
+  if (!Z || !out || n <= 0 || ldz < n) return fail(FOSB_ERR_INVALID_ARG, "fosb_factor: bad arguments");
+  FOSB_TRY(check_prec(prec));
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fosb_lu lu = new (std::nothrow) fosb_lu_s;
+  if (!lu) return fail(FOSB_ERR_OOM, "fosb_factor: host allocation");
+  cudaGetDevice(&lu->device);
+  lu->prec = prec;
+  lu->n = n;
+  const size_t elem = prec == FOSB_FP64 ? 16 : 8;
+  auto cleanup = [&](fosb_status st) {
+    fosb_lu_destroy(lu);
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&lu->lu, elem * n * n);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "fosb_factor: factor storage"));
+  if ((e = cudaMalloc(&lu->ipiv, sizeof(int32_t) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&lu->d_status, sizeof(int) * 2)) != cudaSuccess)
+    return cleanup(cuda_fail(e, "fosb_factor: pivots"));
+  if ((e = cudaMemsetAsync(lu->d_status, 0, sizeof(int) * 2, s)) != cudaSuccess)
+    return cleanup(cuda_fail(e, "fosb_factor"));
+  if (prec == FOSB_FP64)
+    e = copy_matrix(Z, n, n, ldz, lu->lu, n, 16, s);
+  else if (prec == FOSB_MIXED)
+    e = convert_c128_to_c64(Z, n, n, ldz, lu->lu, n, s);
+  else
+    e = copy_matrix(Z, n, n, ldz, lu->lu, n, 8, s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "fosb_factor: copy"));
+  if (prec == FOSB_MIXED) {
+    lu->zref = Z;
+    lu->ldz = ldz;
+    Scratch nrm(s);
+    if ((e = nrm.alloc(sizeof(double))) != cudaSuccess || (e = norm_inf_c128(Z, n, n, ldz, nrm.as<double>(), s)) ||
+        (e = cudaMemcpyAsync(&lu->znorm_inf, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s)))
+      return cleanup(cuda_fail(e, "fosb_factor: norm"));
+  }
+  fosb_status st = prec == FOSB_FP64 ? getrf<double>(lu->lu, n, n, lu->ipiv, lu->d_status, s)
+                                     : getrf<float>(lu->lu, n, n, lu->ipiv, lu->d_status, s);
+  if (st != FOSB_OK) return cleanup(st);
+  int status = 0;
+  std::vector<int32_t> ipiv(n);
+  if ((e = cudaMemcpyAsync(&status, lu->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(ipiv.data(), lu->ipiv, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cleanup(cuda_fail(e, "fosb_factor: status"));
+  if (status == FOSB_ERR_TIMEOUT) return cleanup(fail(FOSB_ERR_TIMEOUT, "fosb_factor: panel grid barrier timed out"));
+  if (status == FOSB_ERR_SINGULAR) return cleanup(fail(FOSB_ERR_SINGULAR, "fosb_factor: zero pivot"));
+  // compose the row interchanges into one permutation: (P b)[i] = b[perm[i]]
+  std::vector<int32_t> perm(n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = int32_t(i);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t p = ipiv[i];
+    if (p < 0 || p >= n) return cleanup(fail(FOSB_ERR_CUDA, "fosb_factor: corrupt pivot"));
+    std::swap(perm[i], perm[p]);
+  }
+  if ((e = cudaMemcpy(lu->ipiv, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice)))
+    return cleanup(cuda_fail(e, "fosb_factor: permutation"));
+  *out = lu;
+  return FOSB_OK;
+}
+
+fosb_status fosb_solve(fosb_lu lu, char op, const void* B, int64_t nrhs, int64_t ldb, void* X, int64_t ldx,
+                       const fosb_refine_opts* ropt, fosb_solve_stats* stats, void* stream) {
+  if (!lu || !B || !X || nrhs < 0 || ldb < nrhs || ldx < nrhs) return fail(FOSB_ERR_INVALID_ARG, "fosb_solve: bad arguments");
+  if (op != 'N' && op != 'n') return fail(FOSB_ERR_INVALID_ARG, "fosb_solve: only op = 'N' is supported");
+  if (X == B && ldx != ldb) return fail(FOSB_ERR_INVALID_ARG, "fosb_solve: aliased X and B need equal leading dimensions");
+  return solve_internal(lu, B, nrhs, ldb, X, ldx, ropt, stats, static_cast<cudaStream_t>(stream));
+}
+
+fosb_status fosb_lu_info(fosb_lu lu, int64_t* n, int* prec, double* znorm_inf) {
+  if (!lu) return fail(FOSB_ERR_INVALID_ARG, "fosb_lu_info: NULL handle");
+  if (n) *n = lu->n;
+  if (prec) *prec = lu->prec;
+  if (znorm_inf) *znorm_inf = lu->znorm_inf;
+  return FOSB_OK;
+}
+
+fosb_status fosb_lu_destroy(fosb_lu lu) {
+  if (!lu) return FOSB_OK;
+  if (lu->lu) cudaFree(lu->lu);
+  if (lu->ipiv) cudaFree(lu->ipiv);
+  if (lu->d_status) cudaFree(lu->d_status);
+  delete lu;
+  return FOSB_OK;
+}
+
+fosb_status fosb_covariance(fosb_mesh m1, fosb_lu lu1, const void* u1, fosb_mesh m2, fosb_lu lu2, const void* u2,
+                            double k, const fosb_cov_kernel* kernel, int pseudo, void* Sigma, int64_t lds,
+                            const fosb_refine_opts* ropt, void* stream) {
+  if (!m1 || !m2 || !lu1 || !lu2 || !u1 || !u2 || !kernel || !Sigma)
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance: NULL argument");
+  if (lu1->prec != lu2->prec) return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance: factor precisions differ");
+  if (lu1->n != m1->d.ne || lu2->n != m2->d.ne) return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance: factor size != mesh edges");
+  if (lds < m2->d.ne) return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance: lds < N2");
+  if (!(k > 0) || !(kernel->ell > 0) || !(kernel->sigma >= 0) || (kernel->kind != FOSB_COV_GAUSS && kernel->kind != FOSB_COV_MATERN32))
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance: bad k or kernel");
+  FOSB_TRY(ensure_rules(5));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int prec = lu1->prec;
+  const bool c64 = is_c64(prec);
+  const size_t elem = c64 ? 8 : 16;
+  const DevMesh& d1 = m1->d;
+  const DevMesh& d2 = m2->d;
+  Scratch b1(s), b2(s), y1(s), y2(s);
+  FOSB_CUDA(b1.alloc(sizeof(double) * 8 * d1.ne));
+  FOSB_CUDA(b2.alloc(sizeof(double) * 8 * d2.ne));
+  FOSB_CUDA(launch_sd_rhs(d1, k, u1, c64, b1.as<double>(), s));
+  FOSB_CUDA(launch_sd_rhs(d2, k, u2, c64, b2.as<double>(), s));
+  // rank r = min(V1, V2): Sigma = (Z1^{-1} L1)(Z2^{-1} L2)^H with L1 = B1 K12, L2 = B2 when V2 <= V1
+  const bool k_on_1 = d2.nv <= d1.nv;
+  const int64_t r = k_on_1 ? d2.nv : d1.nv;
+  FOSB_CUDA(y1.alloc(elem * d1.ne * r));
+  FOSB_CUDA(y2.alloc(elem * d2.ne * r));
+  if (k_on_1) {
+    FOSB_CUDA(launch_bk_product(d1, b1.as<double>(), d2, *kernel, c64, y1.p, r, s));
+    FOSB_CUDA(launch_ell_to_dense(d2, b2.as<double>(), false, c64, y2.p, r, s));
+  } else {
+    FOSB_CUDA(launch_ell_to_dense(d1, b1.as<double>(), false, c64, y1.p, r, s));
+    FOSB_CUDA(launch_bk_product(d2, b2.as<double>(), d1, *kernel, c64, y2.p, r, s));
+  }
+  FOSB_TRY(solve_internal(lu1, y1.p, r, r, y1.p, r, ropt, nullptr, s));
+  FOSB_TRY(solve_internal(lu2, y2.p, r, r, y2.p, r, ropt, nullptr, s));
+  cudaError_t e;
+  if (c64)
+    e = gemm<float>(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
+  else
+    e = gemm<double>(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
+  FOSB_CUDA(e);
+  return FOSB_OK;
+}
+
+fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const double* dirs, int64_t n_dir,
+                                  const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
+                                  int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream) {
+  if (!m1 || !dirs || !X || !out || n_dir <= 0) return fail(FOSB_ERR_INVALID_ARG, "fosb_farfield_moments: NULL argument");
+  FOSB_TRY(check_prec(prec));
+  if (!(k > 0)) return fail(FOSB_ERR_INVALID_ARG, "fosb_farfield_moments: k must be > 0");
+  const int64_t nd3 = 3 * n_dir;
+  if (m2 ? (ldx < m2->d.ne || ldo < nd3) : (ncols <= 0 || ldx < ncols || ldo < ncols))
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_farfield_moments: bad leading dimension");
+  FOSB_TRY(ensure_rules(5));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool c64 = is_c64(prec);
+  const size_t elem = c64 ? 8 : 16;
+  Scratch ddirs(s), a1(s), a2(s), t(s), mm(s);
+  FOSB_CUDA(ddirs.alloc(sizeof(double) * 3 * n_dir));
+  FOSB_CUDA(cudaMemcpyAsync(ddirs.p, dirs, sizeof(double) * 3 * n_dir, cudaMemcpyHostToDevice, s));
+  FOSB_CUDA(a1.alloc(elem * nd3 * m1->d.ne));
+  FOSB_CUDA(cudaMemsetAsync(a1.p, 0, elem * nd3 * m1->d.ne, s));
+  FOSB_CUDA(launch_farfield_matrix(m1->d, k, ddirs.as<double>(), n_dir, c64, a1.p, s));
+  auto G = [&](int opA, int opB, int64_t M, int64_t N, int64_t K, double ar, const void* A, int64_t lda,
+               const void* B, int64_t ldb, double beta, void* C, int64_t ldc) {
+    return c64 ? gemm<float>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s)
+               : gemm<double>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+  };
+  if (!m2) {
+    FOSB_CUDA(G(OP_N, OP_N, nd3, ncols, m1->d.ne, weight, a1.p, m1->d.ne, X, ldx, accumulate ? 1.0 : 0.0, out, ldo));
+    FOSB_CUDA(cudaStreamSynchronize(s));
+    return FOSB_OK;
+  }
+  const int64_t N1 = m1->d.ne, N2 = m2->d.ne;
+  FOSB_CUDA(a2.alloc(elem * nd3 * N2));
+  FOSB_CUDA(cudaMemsetAsync(a2.p, 0, elem * nd3 * N2, s));
+  FOSB_CUDA(launch_farfield_matrix(m2->d, k, ddirs.as<double>(), n_dir, c64, a2.p, s));
+  // T = X op(A2) (N1 x 3 n_dir), M = A1 T
+  FOSB_CUDA(t.alloc(elem * N1 * nd3));
+  FOSB_CUDA(G(OP_N, pseudo ? OP_T : OP_C, N1, nd3, N2, 1.0, X, ldx, a2.p, N2, 0.0, t.p, nd3));
+  if (!hermitian_mirror) {
+    FOSB_CUDA(G(OP_N, OP_N, nd3, nd3, N1, weight, a1.p, N1, t.p, nd3, accumulate ? 1.0 : 0.0, out, ldo));
+  } else {
+    // out = beta out + w (M + op(M)), op = H (covariance) or T (pseudo-covariance)
+    FOSB_CUDA(mm.alloc(elem * nd3 * nd3));
+    FOSB_CUDA(G(OP_N, OP_N, nd3, nd3, N1, 1.0, a1.p, N1, t.p, nd3, 0.0, mm.p, nd3));
+    FOSB_CUDA(add_mirrored(mm.p, nd3, nd3, pseudo ? OP_T : OP_C, weight, accumulate != 0, c64, out, ldo, s));
+  }
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  return FOSB_OK;
+}
+
+}  // extern "C"
+
+// Float-float regular assembly: provided by ff_assemble.cu.

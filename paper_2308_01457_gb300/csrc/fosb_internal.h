@@ -1,0 +1,139 @@
+// Internal declarations of the FOSB library (host + device).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fosb.h"
+
+namespace fosb {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+fosb_status fail(fosb_status code, const std::string& msg);
+fosb_status cuda_fail(cudaError_t e, const char* where);
+
+#define FOSB_CUDA(call)                                       \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return fosb::cuda_fail(e_, #call); \
+  } while (0)
+
+#define FOSB_TRY(call)                    \
+  do {                                    \
+    fosb_status s_ = (call);              \
+    if (s_ != FOSB_OK) return s_;         \
+  } while (0)
+
+// ---------------------------------------------------------------- mesh
+// Touching triangle pair in Sauter-Schwab orientation: x triangle t1 with its vertex
+// order p[3], y triangle t2 with q[3]; kind 1 = vertex, 2 = edge, 3 = identical.
+struct TouchPair {
+  int32_t t1, t2, kind, pad;
+  int32_t p[3], q[3];
+};
+
+// Per-triangle record (device, structure of arrays).  Local edge i is opposite local
+// vertex i.
+struct DevMesh {
+  int64_t nv = 0, nt = 0, ne = 0, ntouch = 0;
+  double* verts = nullptr;      // nv x 3
+  double* vnormals = nullptr;   // nv x 3
+  int32_t* tris = nullptr;      // nt x 3
+  int32_t* tri_edge = nullptr;  // nt x 3
+  double* tri_coef = nullptr;   // nt x 3: s l / (2A)
+  double* tri_div = nullptr;    // nt x 3: s l / A
+  double* tri_area = nullptr;   // nt
+  double* tri_normal = nullptr; // nt x 3 unit normals
+  double* tri_qp = nullptr;     // nt x 18: the 6 quadrature points (x, y, z)
+  TouchPair* touch = nullptr;   // ntouch
+  int32_t* ell_cols = nullptr;  // ne x 4: vertices a, b of edge m, opposite vertex in T+, in T-
+};
+
+}  // namespace fosb
+
+struct fosb_mesh_s {
+  int device = 0;
+  std::vector<double> verts, vnormals;
+  std::vector<int32_t> tris;
+  std::vector<int32_t> edges;      // ne x 2
+  std::vector<int32_t> edge_tris;  // ne x 2 (T+, T-)
+  std::vector<int32_t> tri_edge;   // nt x 3
+  std::vector<double> tri_sign;    // nt x 3
+  std::vector<fosb::TouchPair> touch;
+  fosb::DevMesh d;
+};
+
+struct fosb_lu_s {
+  int device = 0;
+  int prec = 0;
+  int64_t n = 0;
+  void* lu = nullptr;          // n x n factors (complex128 for FP64, complex64 otherwise), row-major ld = n
+  int32_t* ipiv = nullptr;     // n pivots (row swapped with i at step i), device
+  const void* zref = nullptr;  // MIXED: non-owning complex128 Z for residuals
+  int64_t ldz = 0;
+  double znorm_inf = 0.0;      // ||Z||_inf (FP64)
+  int* d_status = nullptr;     // device status word
+};
+
+namespace fosb {
+
+// ---------------------------------------------------------------- quadrature rules
+struct Rules {
+  double bary[6][3];
+  double w[6];
+  int nss;
+  double glx[16], glw[16];
+};
+Rules make_rules(int nss);
+
+// ---------------------------------------------------------------- kernels (launchers)
+// Assembly
+cudaError_t launch_assemble_regular(const DevMesh& m, double k, int arith, void* Z, int64_t ldz, cudaStream_t s);
+cudaError_t launch_assemble_singular(const DevMesh& m, double k, int nss, bool fp32_out, void* Z, int64_t ldz,
+                                     cudaStream_t s);
+cudaError_t launch_rhs(const DevMesh& m, double k, const double* d_inc, int64_t n_inc, bool fp32_out, void* b,
+                       int64_t ldb, cudaStream_t s);
+void upload_rules(const Rules& r);
+cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_t ldz, cudaStream_t s);
+
+// Far field
+cudaError_t launch_farfield_matrix(const DevMesh& m, double k, const double* d_dirs, int64_t n_dir, bool fp32,
+                                   void* A, cudaStream_t s);
+
+// Shape-derivative RHS in ELL form (N x 4 complex128 values on the columns ell_cols),
+// its dense expansion (N x V), and W = B1 K12 (N1 x V2) with K evaluated on the fly.
+cudaError_t launch_sd_rhs(const DevMesh& m, double k, const void* u, bool u_fp32, double* B_ell, cudaStream_t s);
+cudaError_t launch_ell_to_dense(const DevMesh& m, const double* B_ell, bool conj_out, bool fp32, void* B, int64_t ldb,
+                                cudaStream_t s);
+cudaError_t launch_bk_product(const DevMesh& m1, const double* B1_ell, const DevMesh& m2,
+                              const fosb_cov_kernel& ker, bool fp32, void* W, int64_t ldw, cudaStream_t s);
+
+// Dense complex linear algebra (row-major).  T = double or float.
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2 };
+template <typename T>
+cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im, const void* A,
+                 int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s);
+template <typename T>
+fosb_status getrf(void* A, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, cudaStream_t s);
+template <typename T>
+cudaError_t getrs(const void* LU, int64_t n, int64_t ldlu, const int32_t* ipiv, void* X, int64_t nrhs, int64_t ldx,
+                  cudaStream_t s);
+cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                                cudaStream_t s);
+cudaError_t convert_c64_to_c128(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                                cudaStream_t s);
+cudaError_t copy_matrix(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd, size_t elem,
+                        cudaStream_t s);
+cudaError_t axpy_c64_into_c128(const void* d, int64_t rows, int64_t cols, int64_t ldd, void* x, int64_t ldx,
+                               cudaStream_t s);
+// out = (accumulate ? out : 0) + w (M + op(M)) for a square n x n matrix M (op = OP_T or OP_C)
+cudaError_t add_mirrored(const void* M, int64_t n, int64_t ldm, int op, double w, bool accumulate, bool c64, void* out,
+                         int64_t ldo, cudaStream_t s);
+// row-wise inf-norm reductions: out[0] = max_i sum_j |Re|+|Im| (matrix), or max |.|
+cudaError_t norm_inf_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s);
+cudaError_t absmax_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s);
+
+}  // namespace fosb

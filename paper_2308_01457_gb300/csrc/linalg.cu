@@ -1,0 +1,699 @@
+// Dense complex linear algebra for the EFIE systems (row-major, interleaved complex).
+//
+//   * gemm: C = alpha op(A) op(B) + beta C, complex128 or complex64.  A 64 x 64 tiled SIMT
+//     kernel for wide products and a row-per-warp kernel for skinny products
+//     (<= 8 right-hand sides), which streams A once at HBM speed (IR residuals).
+//   * getrf: blocked right-looking LU with partial pivoting.  The panel is factored by a
+//     cooperative kernel whose CTAs own row chunks and meet at a software grid barrier
+//     once per column (bounded spin: on time-out the status word is set and the kernel
+//     returns).  Row swaps, the unit-lower triangular solve of the block row and the
+//     trailing update (gemm) follow.
+//   * getrs: forward / backward substitution by diagonal-block solves plus gemm updates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "fosb_internal.h"
+
+namespace fosb {
+namespace {
+
+template <typename T>
+struct C2;
+template <>
+struct C2<double> {
+  using type = double2;
+};
+template <>
+struct C2<float> {
+  using type = float2;
+};
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a, typename C2<T>::type b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::type load_op(const typename C2<T>::type* P, int64_t r, int64_t c, int64_t ld,
+                                                        int op) {
+  // element (r, c) of op(P): N -> P[r, c]; T -> P[c, r]; C -> conj(P[c, r])
+  typename C2<T>::type v = (op == OP_N) ? P[r * ld + c] : P[c * ld + r];
+  if (op == OP_C) v.y = -v.y;
+  return v;
+}
+
+inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ tiled GEMM
+constexpr int TBM = 64, TBN = 64, TBK = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_tiled_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, T ar, T ai,
+                                                         const typename C2<T>::type* __restrict__ A, int64_t lda,
+                                                         const typename C2<T>::type* __restrict__ B, int64_t ldb, T beta,
+                                                         typename C2<T>::type* __restrict__ C, int64_t ldc) {
+  using V = typename C2<T>::type;
+  __shared__ V As[TBK][TBM + 1];
+  __shared__ V Bs[TBK][TBN + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t row0 = int64_t(blockIdx.y) * TBM, col0 = int64_t(blockIdx.x) * TBN;
+  V acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = {T(0), T(0)};
+  for (int64_t k0 = 0; k0 < K; k0 += TBK) {
+    // A tile: 64 rows x 8 k (2 elements per thread)
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      int e = tid + 256 * l;
+      int r, kk;
+      if (opA == OP_N) {
+        r = e / TBK;
+        kk = e % TBK;
+      } else {
+        kk = e / TBM;
+        r = e % TBM;
+      }
+      int64_t gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? load_op<T>(A, gr, gk, lda, opA) : V{T(0), T(0)};
+    }
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      int e = tid + 256 * l;
+      int c, kk;
+      if (opB == OP_N) {
+        kk = e / TBN;
+        c = e % TBN;
+      } else {
+        c = e / TBK;
+        kk = e % TBK;
+      }
+      int64_t gc = col0 + c, gk = k0 + kk;
+      Bs[kk][c] = (gc < N && gk < K) ? load_op<T>(B, gk, gc, ldb, opB) : V{T(0), T(0)};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TBK; ++kk) {
+      V a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
+          acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t r = row0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t c = col0 + tx + 16 * j;
+      if (c >= N) continue;
+      V v = {ar * acc[i][j].x - ai * acc[i][j].y, ar * acc[i][j].y + ai * acc[i][j].x};
+      if (beta != T(0)) {
+        V o = C[r * ldc + c];
+        v.x += beta * o.x;
+        v.y += beta * o.y;
+      }
+      C[r * ldc + c] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ skinny GEMM (op(A) = A)
+// One warp per row of A; lanes stride over K; N <= 8 columns of op(B).
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) gemm_skinny_kernel(int opB, int64_t M, int64_t K, T ar, T ai,
+                                                          const typename C2<T>::type* __restrict__ A, int64_t lda,
+                                                          const typename C2<T>::type* __restrict__ B, int64_t ldb,
+                                                          T beta, typename C2<T>::type* __restrict__ C, int64_t ldc) {
+  using V = typename C2<T>::type;
+  const int64_t row = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  V acc[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] = {T(0), T(0)};
+  const V* arow = A + row * lda;
+  for (int64_t k = lane; k < K; k += 32) {
+    V a = arow[k];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      V b = load_op<T>(B, k, j, ldb, opB);
+      acc[j].x = fma(a.x, b.x, acc[j].x);
+      acc[j].x = fma(-a.y, b.y, acc[j].x);
+      acc[j].y = fma(a.x, b.y, acc[j].y);
+      acc[j].y = fma(a.y, b.x, acc[j].y);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, off);
+      acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, off);
+    }
+  }
+  if (lane < NC) {
+    V s = acc[0];
+#pragma unroll
+    for (int j = 1; j < NC; ++j)
+      if (lane == j) s = acc[j];
+    V v = {ar * s.x - ai * s.y, ar * s.y + ai * s.x};
+    if (beta != T(0)) {
+      V o = C[row * ldc + lane];
+      v.x += beta * o.x;
+      v.y += beta * o.y;
+    }
+    C[row * ldc + lane] = v;
+  }
+}
+
+// ------------------------------------------------------------------ panel factorisation
+struct PanelScratch {
+  unsigned count;
+  unsigned gen;
+};
+
+constexpr int kPanelThreads = 256;
+constexpr int kMaxPanelRows = 2048;  // rows per CTA (multipliers kept in shared memory)
+constexpr long long kSpinLimit = 1ll << 26;
+
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = gen;
+    unsigned my_gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == my_gen) {
+        if (++spins > kSpinLimit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
+          atomicExch(status, FOSB_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// cand_val[2][G], cand_row[2][G], cand_data[2][G][jb], rowj[2][jb]
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::type* A, int64_t m, int jb, int64_t lda,
+                                                              int32_t* ipiv, int64_t row_base, PanelScratch* scr,
+                                                              double* cand_val, int64_t* cand_row,
+                                                              typename C2<T>::type* cand_data,
+                                                              typename C2<T>::type* rowj, int* status) {
+  using V = typename C2<T>::type;
+  const unsigned G = gridDim.x;
+  const int64_t chunk = (m + G - 1) / G;
+  const int64_t lo = int64_t(blockIdx.x) * chunk, hi = min(m, lo + chunk);
+  __shared__ double s_val[kPanelThreads / 32];
+  __shared__ int64_t s_row[kPanelThreads / 32];
+  __shared__ V s_l[kMaxPanelRows];
+  __shared__ V s_piv[64];
+  __shared__ int64_t s_p;
+  __shared__ int s_win;
+  for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
+    // 1. local pivot candidate (largest |Re|+|Im|, ties -> lowest row)
+    double best = -1.0;
+    int64_t brow = m;
+    for (int64_t r = max(lo, int64_t(j)) + threadIdx.x; r < hi; r += blockDim.x) {
+      V v = A[r * lda + j];
+      double a = fabs(double(v.x)) + fabs(double(v.y));
+      if (a > best) {
+        best = a;
+        brow = r;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, off);
+      int64_t orow = __shfl_xor_sync(0xffffffffu, brow, off);
+      if (ob > best || (ob == best && orow < brow)) {
+        best = ob;
+        brow = orow;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_val[threadIdx.x >> 5] = best;
+      s_row[threadIdx.x >> 5] = brow;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kPanelThreads / 32; ++w)
+        if (s_val[w] > best || (s_val[w] == best && s_row[w] < brow)) {
+          best = s_val[w];
+          brow = s_row[w];
+        }
+      s_val[0] = best;
+      s_row[0] = brow;
+    }
+    __syncthreads();
+    best = s_val[0];
+    brow = s_row[0];
+    // 2. publish the candidate (value, row and its panel row) and, by its owner, row j
+    if (threadIdx.x == 0) {
+      cand_val[par * G + blockIdx.x] = best;
+      cand_row[par * G + blockIdx.x] = brow;
+    }
+    for (int c = threadIdx.x; c < jb; c += blockDim.x) {
+      cand_data[(int64_t(par) * G + blockIdx.x) * jb + c] = (brow < m) ? A[brow * lda + c] : V{T(0), T(0)};
+      if (j >= lo && j < hi) rowj[par * jb + c] = A[int64_t(j) * lda + c];
+    }
+    __threadfence();
+    if (!grid_barrier(&scr->count, &scr->gen, G, status)) return;
+    // 3. global pivot: every CTA reduces the G candidates identically
+    if (threadIdx.x < 32) {
+      double b = -1.0;
+      int64_t r = m;
+      int win = 0;
+      for (unsigned g = threadIdx.x; g < G; g += 32) {
+        double v = ((volatile double*)cand_val)[par * G + g];
+        int64_t rr = ((volatile int64_t*)cand_row)[par * G + g];
+        if (v > b || (v == b && rr < r)) {
+          b = v;
+          r = rr;
+          win = int(g);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, b, off);
+        int64_t orow = __shfl_xor_sync(0xffffffffu, r, off);
+        int ow = __shfl_xor_sync(0xffffffffu, win, off);
+        if (ob > b || (ob == b && orow < r)) {
+          b = ob;
+          r = orow;
+          win = ow;
+        }
+      }
+      if (threadIdx.x == 0) {
+        s_p = r;
+        s_win = win;
+        if (blockIdx.x == 0) {
+          ipiv[j] = int32_t(row_base + r);
+          if (!(b > 0.0)) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    const V* pdata = cand_data + (int64_t(par) * G + s_win) * jb;
+    for (int c = threadIdx.x; c < jb; c += blockDim.x) s_piv[c] = __ldcg(pdata + c);
+    __syncthreads();
+    // 4. swap rows j and p inside the panel
+    if (p != j) {
+      if (j >= lo && j < hi)
+        for (int c = threadIdx.x; c < jb; c += blockDim.x) A[int64_t(j) * lda + c] = s_piv[c];
+      if (p >= lo && p < hi)
+        for (int c = threadIdx.x; c < jb; c += blockDim.x) A[p * lda + c] = __ldcg(rowj + par * jb + c);
+    }
+    __syncthreads();
+    // 5. multipliers and rank-1 update of the rows below j owned by this CTA
+    const V pv = s_piv[j];
+    const T den = pv.x * pv.x + pv.y * pv.y;
+    const V inv = den > T(0) ? V{pv.x / den, -pv.y / den} : V{T(0), T(0)};
+    const int64_t r0 = max(lo, int64_t(j) + 1);
+    for (int64_t r = r0 + threadIdx.x; r < hi; r += blockDim.x) {
+      V l = cmul<T>(A[r * lda + j], inv);
+      A[r * lda + j] = l;
+      s_l[r - lo] = l;
+    }
+    __syncthreads();
+    const int ncols = jb - j - 1;
+    if (ncols > 0 && hi > r0) {
+      const int64_t total = (hi - r0) * ncols;
+      for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        int64_t r = r0 + e / ncols;
+        int c = j + 1 + int(e % ncols);
+        V l = s_l[r - lo], u = s_piv[c];
+        V a = A[r * lda + c];
+        a.x -= l.x * u.x - l.y * u.y;
+        a.y -= l.x * u.y + l.y * u.x;
+        A[r * lda + c] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Row swaps of the block row [j0, j0 + jb) applied to columns outside the panel.
+template <typename T>
+__global__ void laswp_kernel(typename C2<T>::type* A, int64_t n, int64_t lda, int64_t j0, int jb,
+                             const int32_t* ipiv) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= n || (c >= j0 && c < j0 + jb)) return;
+  for (int i = 0; i < jb; ++i) {
+    int64_t p = ipiv[j0 + i];
+    if (p != j0 + i) {
+      auto t = A[(j0 + i) * lda + c];
+      A[(j0 + i) * lda + c] = A[p * lda + c];
+      A[p * lda + c] = t;
+    }
+  }
+}
+
+// X (nb x ncols block) <- L^{-1} X with L unit lower (unit=1) or U^{-1} X with U upper
+// (unit=0), diagonal block of size nb at D (leading dimension ldd).  Thread per column.
+template <typename T>
+__global__ void trsm_diag_kernel(const typename C2<T>::type* D, int64_t ldd, int nb, int upper,
+                                 typename C2<T>::type* X, int64_t ldx, int64_t ncols) {
+  using V = typename C2<T>::type;
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  if (!upper) {
+    for (int i = 1; i < nb; ++i) {
+      V s = X[int64_t(i) * ldx + c];
+      for (int k = 0; k < i; ++k) {
+        V l = D[int64_t(i) * ldd + k], x = X[int64_t(k) * ldx + c];
+        s.x -= l.x * x.x - l.y * x.y;
+        s.y -= l.x * x.y + l.y * x.x;
+      }
+      X[int64_t(i) * ldx + c] = s;
+    }
+  } else {
+    for (int i = nb - 1; i >= 0; --i) {
+      V s = X[int64_t(i) * ldx + c];
+      for (int k = i + 1; k < nb; ++k) {
+        V u = D[int64_t(i) * ldd + k], x = X[int64_t(k) * ldx + c];
+        s.x -= u.x * x.x - u.y * x.y;
+        s.y -= u.x * x.y + u.y * x.x;
+      }
+      V d = D[int64_t(i) * ldd + i];
+      T den = d.x * d.x + d.y * d.y;
+      V q = den > T(0) ? V{(s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den} : V{T(0), T(0)};
+      X[int64_t(i) * ldx + c] = q;
+    }
+  }
+}
+
+template <typename T>
+__global__ void gather_rows_kernel(const typename C2<T>::type* X, int64_t ldx, const int32_t* perm, int64_t n,
+                                   int64_t nrhs, typename C2<T>::type* Y, int64_t ldy) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * nrhs) return;
+  int64_t i = e / nrhs, c = e % nrhs;
+  Y[i * ldy + c] = X[int64_t(perm[i]) * ldx + c];
+}
+
+__global__ void c128_to_c64_kernel(const double2* s, int64_t rows, int64_t cols, int64_t lds, float2* d, int64_t ldd) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t i = e / cols, j = e % cols;
+  double2 v = s[i * lds + j];
+  d[i * ldd + j] = make_float2(float(v.x), float(v.y));
+}
+__global__ void c64_to_c128_kernel(const float2* s, int64_t rows, int64_t cols, int64_t lds, double2* d, int64_t ldd) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t i = e / cols, j = e % cols;
+  float2 v = s[i * lds + j];
+  d[i * ldd + j] = make_double2(v.x, v.y);
+}
+__global__ void axpy_kernel(const float2* dlt, int64_t rows, int64_t cols, int64_t ldd, double2* x, int64_t ldx) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t i = e / cols, j = e % cols;
+  float2 v = dlt[i * ldd + j];
+  x[i * ldx + j].x += v.x;
+  x[i * ldx + j].y += v.y;
+}
+
+__device__ __forceinline__ void atomic_max_pos(double* p, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(p), __double_as_longlong(v));
+}
+
+__global__ void row_norm_kernel(const double2* A, int64_t rows, int64_t cols, int64_t lda, double* out) {
+  int64_t r = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  double s = 0;
+  for (int64_t c = lane; c < cols; c += 32) {
+    double2 v = A[r * lda + c];
+    s += fabs(v.x) + fabs(v.y);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) atomic_max_pos(out, s);
+}
+
+// per-column max |Re| + |Im| (out has cols entries)
+__global__ void col_absmax_kernel(const double2* A, int64_t rows, int64_t cols, int64_t lda, double* out) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t i = e / cols, j = e % cols;
+  double2 v = A[i * lda + j];
+  atomic_max_pos(out + j, fabs(v.x) + fabs(v.y));
+}
+
+template <typename T>
+__global__ void add_mirrored_kernel(const typename C2<T>::type* M, int64_t n, int64_t ldm, int op, T w, int acc,
+                                    typename C2<T>::type* out, int64_t ldo) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  int64_t i = e / n, j = e % n;
+  auto a = M[i * ldm + j], b = M[j * ldm + i];
+  if (op == OP_C) b.y = -b.y;
+  typename C2<T>::type v = {w * (a.x + b.x), w * (a.y + b.y)};
+  if (acc) {
+    v.x += out[i * ldo + j].x;
+    v.y += out[i * ldo + j].y;
+  }
+  out[i * ldo + j] = v;
+}
+
+template <typename T>
+__global__ void copy_kernel(const T* s, int64_t rows, int64_t cols, int64_t lds, T* d, int64_t ldd) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  int64_t i = e / cols, j = e % cols;
+  d[i * ldd + j] = s[i * lds + j];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im, const void* A,
+                 int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s) {
+  using V = typename C2<T>::type;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0) {
+    // C = beta C
+    if (beta == 0.0) return cudaMemset2DAsync(C, ldc * sizeof(V), 0, N * sizeof(V), M, s);
+    return cudaSuccess;
+  }
+  const V* a = static_cast<const V*>(A);
+  const V* b = static_cast<const V*>(B);
+  V* c = static_cast<V*>(C);
+  if (opA == OP_N && N <= 8) {
+    unsigned g = cdiv(M, 8);
+#define FOSB_SKINNY(NC) \
+  gemm_skinny_kernel<T, NC><<<g, 256, 0, s>>>(opB, M, K, T(alpha_re), T(alpha_im), a, lda, b, ldb, T(beta), c, ldc)
+    switch (N) {
+      case 1: FOSB_SKINNY(1); break;
+      case 2: FOSB_SKINNY(2); break;
+      case 3: FOSB_SKINNY(3); break;
+      case 4: FOSB_SKINNY(4); break;
+      case 5: FOSB_SKINNY(5); break;
+      case 6: FOSB_SKINNY(6); break;
+      case 7: FOSB_SKINNY(7); break;
+      default: FOSB_SKINNY(8); break;
+    }
+#undef FOSB_SKINNY
+    return cudaGetLastError();
+  }
+  if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
+  dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
+  gemm_tiled_kernel<T><<<grid, 256, 0, s>>>(opA, opB, M, N, K, T(alpha_re), T(alpha_im), a, lda, b, ldb, T(beta), c, ldc);
+  return cudaGetLastError();
+}
+
+template cudaError_t gemm<double>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
+                                  const void*, int64_t, double, void*, int64_t, cudaStream_t);
+template cudaError_t gemm<float>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
+                                 const void*, int64_t, double, void*, int64_t, cudaStream_t);
+
+template <typename T>
+fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, cudaStream_t s) {
+  using V = typename C2<T>::type;
+  V* A = static_cast<V*>(Av);
+  const int nb = 64;
+  int dev = 0, nsm = 0;
+  FOSB_CUDA(cudaGetDevice(&dev));
+  FOSB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int per_sm = 0;
+  FOSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<T>, kPanelThreads, 0));
+  if (per_sm < 1) return fail(FOSB_ERR_CUDA, "getrf: panel kernel cannot be resident");
+  const int gmax = nsm * per_sm;
+  // scratch: barrier + candidates
+  size_t G_cap = size_t(std::min<int64_t>(gmax, std::max<int64_t>(1, (n + 63) / 64)));
+  size_t bytes = 256 + 2 * G_cap * (sizeof(double) + sizeof(int64_t)) + 2 * G_cap * nb * sizeof(V) + 2 * nb * sizeof(V);
+  char* scratch = nullptr;
+  FOSB_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s));
+  FOSB_CUDA(cudaMemsetAsync(scratch, 0, 256, s));
+  PanelScratch* scr = reinterpret_cast<PanelScratch*>(scratch);
+  double* cand_val = reinterpret_cast<double*>(scratch + 256);
+  int64_t* cand_row = reinterpret_cast<int64_t*>(cand_val + 2 * G_cap);
+  V* cand_data = reinterpret_cast<V*>(cand_row + 2 * G_cap);
+  V* rowj = cand_data + 2 * G_cap * nb;
+  fosb_status st = FOSB_OK;
+  for (int64_t j0 = 0; j0 < n && st == FOSB_OK; j0 += nb) {
+    int jb = int(std::min<int64_t>(nb, n - j0));
+    int64_t m = n - j0;
+    int64_t G = std::min<int64_t>(int64_t(G_cap), std::max<int64_t>(1, (m + 63) / 64));
+    if ((m + G - 1) / G > kMaxPanelRows) {
+      st = fail(FOSB_ERR_INVALID_ARG, "getrf: matrix too large for the panel kernel");
+      break;
+    }
+    V* Ap = A + j0 * lda + j0;
+    int32_t* ip = ipiv + j0;
+    int64_t base = j0;
+    void* args[] = {&Ap, &m, &jb, &lda, &ip, &base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
+    cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)),
+                                                dim3(kPanelThreads), args, 0, s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "getrf: cooperative panel launch");
+      break;
+    }
+    laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
+    int64_t rest = n - j0 - jb;
+    if (rest > 0) {
+      trsm_diag_kernel<T><<<cdiv(rest, 128), 128, 0, s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
+      e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0, Ap + jb * lda + jb, lda, s);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "getrf: trailing update");
+        break;
+      }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "getrf");
+  }
+  cudaFreeAsync(scratch, s);
+  return st;
+}
+
+template fosb_status getrf<double>(void*, int64_t, int64_t, int32_t*, int*, cudaStream_t);
+template fosb_status getrf<float>(void*, int64_t, int64_t, int32_t*, int*, cudaStream_t);
+
+// X <- Z^{-1} X given the factors (perm = composed row permutation, device).
+template <typename T>
+cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm, void* Xv, int64_t nrhs, int64_t ldx,
+                  cudaStream_t s) {
+  using V = typename C2<T>::type;
+  const V* LU = static_cast<const V*>(LUv);
+  V* X = static_cast<V*>(Xv);
+  V* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(V) * n * nrhs, s);
+  if (e != cudaSuccess) return e;
+  gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
+  const int nb = 64;
+  // forward: unit lower
+  for (int64_t i0 = 0; i0 < n; i0 += nb) {
+    int ib = int(std::min<int64_t>(nb, n - i0));
+    trsm_diag_kernel<T><<<cdiv(nrhs, 128), 128, 0, s>>>(LU + i0 * ldlu + i0, ldlu, ib, 0, tmp + i0 * nrhs, nrhs, nrhs);
+    int64_t rest = n - i0 - ib;
+    if (rest > 0) {
+      e = gemm<T>(OP_N, OP_N, rest, nrhs, ib, -1.0, 0.0, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0,
+                  tmp + (i0 + ib) * nrhs, nrhs, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  // backward: upper
+  for (int64_t i1 = n; i1 > 0; i1 -= nb) {
+    int64_t i0 = std::max<int64_t>(0, i1 - nb);
+    int ib = int(i1 - i0);
+    trsm_diag_kernel<T><<<cdiv(nrhs, 128), 128, 0, s>>>(LU + i0 * ldlu + i0, ldlu, ib, 1, tmp + i0 * nrhs, nrhs, nrhs);
+    if (i0 > 0) {
+      e = gemm<T>(OP_N, OP_N, i0, nrhs, ib, -1.0, 0.0, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0, tmp, nrhs, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  copy_kernel<V><<<cdiv(n * nrhs, 256), 256, 0, s>>>(tmp, n, nrhs, nrhs, X, ldx);
+  cudaFreeAsync(tmp, s);
+  return cudaGetLastError();
+}
+
+template cudaError_t getrs<double>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t);
+template cudaError_t getrs<float>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t);
+
+cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                                cudaStream_t s) {
+  if (rows * cols == 0) return cudaSuccess;
+  c128_to_c64_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const double2*>(src), rows, cols, lds,
+                                                            static_cast<float2*>(dst), ldd);
+  return cudaGetLastError();
+}
+cudaError_t convert_c64_to_c128(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                                cudaStream_t s) {
+  if (rows * cols == 0) return cudaSuccess;
+  c64_to_c128_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const float2*>(src), rows, cols, lds,
+                                                            static_cast<double2*>(dst), ldd);
+  return cudaGetLastError();
+}
+cudaError_t copy_matrix(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd, size_t elem,
+                        cudaStream_t s) {
+  return cudaMemcpy2DAsync(dst, ldd * elem, src, lds * elem, cols * elem, rows, cudaMemcpyDeviceToDevice, s);
+}
+cudaError_t axpy_c64_into_c128(const void* d, int64_t rows, int64_t cols, int64_t ldd, void* x, int64_t ldx,
+                               cudaStream_t s) {
+  if (rows * cols == 0) return cudaSuccess;
+  axpy_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const float2*>(d), rows, cols, ldd,
+                                                     static_cast<double2*>(x), ldx);
+  return cudaGetLastError();
+}
+cudaError_t add_mirrored(const void* M, int64_t n, int64_t ldm, int op, double w, bool accumulate, bool c64, void* out,
+                         int64_t ldo, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (c64)
+    add_mirrored_kernel<float><<<cdiv(n * n, 256), 256, 0, s>>>(static_cast<const float2*>(M), n, ldm, op, float(w),
+                                                                accumulate, static_cast<float2*>(out), ldo);
+  else
+    add_mirrored_kernel<double><<<cdiv(n * n, 256), 256, 0, s>>>(static_cast<const double2*>(M), n, ldm, op, w,
+                                                                 accumulate, static_cast<double2*>(out), ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t norm_inf_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  row_norm_kernel<<<cdiv(rows, 8), 256, 0, s>>>(static_cast<const double2*>(A), rows, cols, lda, d_out);
+  return cudaGetLastError();
+}
+cudaError_t absmax_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * cols, s);
+  if (e != cudaSuccess) return e;
+  if (rows * cols == 0) return cudaSuccess;
+  col_absmax_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const double2*>(A), rows, cols, lda, d_out);
+  return cudaGetLastError();
+}
+
+}  // namespace fosb
