@@ -106,6 +106,10 @@ const char* fosb_last_error(void);
 /* Library version string. */
 const char* fosb_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all devices);
+ * diagnostics for launch accounting. */
+uint64_t fosb_kernel_launches(void);
+
 /* ---- A1: mesh tables ------------------------------------------------------------
  * Builds the RWG tables of a closed, orientable, manifold triangulation (Section IV,
  * meshes Gamma_{h_l} of planar triangles) and uploads them to the current device.

@@ -63,6 +63,7 @@ def lib():
         L = ctypes.CDLL(path)
         L.fosb_last_error.restype = ctypes.c_char_p
         L.fosb_version.restype = ctypes.c_char_p
+        L.fosb_kernel_launches.restype = ctypes.c_uint64
         for name in ("fosb_mesh_create", "fosb_mesh_info", "fosb_mesh_edges", "fosb_mesh_destroy",
                      "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
                      "fosb_covariance", "fosb_farfield_moments"):

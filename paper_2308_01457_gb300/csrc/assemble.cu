@@ -496,7 +496,7 @@ cudaError_t launch_assemble_regular(const DevMesh& m, double k, int arith, void*
   } else {
     efie_regular_kernel<float, float><<<grid, 256, 0, s>>>(m, k, static_cast<float*>(Z), ldz);
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_assemble_singular(const DevMesh& m, double k, int nss, bool fp32_out, void* Z, int64_t ldz,
@@ -506,7 +506,7 @@ cudaError_t launch_assemble_singular(const DevMesh& m, double k, int nss, bool f
     efie_singular_kernel<float><<<unsigned(m.ntouch), 128, 0, s>>>(m, k, nss, static_cast<float*>(Z), ldz);
   else
     efie_singular_kernel<double><<<unsigned(m.ntouch), 128, 0, s>>>(m, k, nss, static_cast<double*>(Z), ldz);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_rhs(const DevMesh& m, double k, const double* d_inc, int64_t n_inc, bool fp32_out, void* b,
@@ -517,7 +517,7 @@ cudaError_t launch_rhs(const DevMesh& m, double k, const double* d_inc, int64_t 
     rhs_kernel<float><<<g, 128, 0, s>>>(m, k, d_inc, n_inc, static_cast<float*>(b), ldb);
   else
     rhs_kernel<double><<<g, 128, 0, s>>>(m, k, d_inc, n_inc, static_cast<double*>(b), ldb);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_farfield_matrix(const DevMesh& m, double k, const double* d_dirs, int64_t n_dir, bool fp32,
@@ -527,7 +527,7 @@ cudaError_t launch_farfield_matrix(const DevMesh& m, double k, const double* d_d
     farfield_kernel<float><<<g, 128, 0, s>>>(m, k, d_dirs, n_dir, static_cast<float*>(A));
   else
     farfield_kernel<double><<<g, 128, 0, s>>>(m, k, d_dirs, n_dir, static_cast<double*>(A));
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_sd_rhs(const DevMesh& m, double k, const void* u, bool u_fp32, double* B_ell, cudaStream_t s) {
@@ -537,7 +537,7 @@ cudaError_t launch_sd_rhs(const DevMesh& m, double k, const void* u, bool u_fp32
     sd_rhs_kernel<float><<<blocks_for(m.nt, 128), 128, 0, s>>>(m, k, static_cast<const float*>(u), B_ell);
   else
     sd_rhs_kernel<double><<<blocks_for(m.nt, 128), 128, 0, s>>>(m, k, static_cast<const double*>(u), B_ell);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_ell_to_dense(const DevMesh& m, const double* B_ell, bool conj_out, bool fp32, void* B, int64_t ldb,
@@ -549,7 +549,7 @@ cudaError_t launch_ell_to_dense(const DevMesh& m, const double* B_ell, bool conj
     ell_to_dense_kernel<float><<<blocks_for(m.ne, 128), 128, 0, s>>>(m, B_ell, conj_out, static_cast<float*>(B), ldb);
   else
     ell_to_dense_kernel<double><<<blocks_for(m.ne, 128), 128, 0, s>>>(m, B_ell, conj_out, static_cast<double*>(B), ldb);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_bk_product(const DevMesh& m1, const double* B1_ell, const DevMesh& m2, const fosb_cov_kernel& ker,
@@ -560,7 +560,7 @@ cudaError_t launch_bk_product(const DevMesh& m1, const double* B1_ell, const Dev
     bk_product_kernel<float><<<grid, 128, 0, s>>>(m1, B1_ell, m2, ker.kind, ker.sigma, ker.ell, static_cast<float*>(W), ldw);
   else
     bk_product_kernel<double><<<grid, 128, 0, s>>>(m1, B1_ell, m2, ker.kind, ker.sigma, ker.ell, static_cast<double*>(W), ldw);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace fosb

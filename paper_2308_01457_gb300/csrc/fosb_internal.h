@@ -21,6 +21,13 @@ fosb_status cuda_fail(cudaError_t e, const char* where);
     if (e_ != cudaSuccess) return fosb::cuda_fail(e_, #call); \
   } while (0)
 
+// Count of kernels this library has launched (diagnostics: fosb_kernel_launches).
+void note_launches(uint64_t n);
+inline cudaError_t launched(uint64_t n = 1) {
+  note_launches(n);
+  return cudaGetLastError();
+}
+
 #define FOSB_TRY(call)                    \
   do {                                    \
     fosb_status s_ = (call);              \

@@ -415,6 +415,62 @@ __global__ void trsm_diag_kernel(const typename C2<T>::type* D, int64_t ldd, int
   }
 }
 
+// Few right-hand sides: one warp per column, lanes own rows (lane, lane + 32) of the
+// nb x nb diagonal block, which is staged transposed in shared memory (conflict-free
+// column reads).  Forward (unit lower) or backward (upper, with the diagonal) sweep.
+template <typename T>
+__global__ void __launch_bounds__(256) trsv_warp_kernel(const typename C2<T>::type* D, int64_t ldd, int nb, int upper,
+                                                        typename C2<T>::type* X, int64_t ldx, int64_t ncols) {
+  using V = typename C2<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  V* Dt = reinterpret_cast<V*>(smem_raw);  // Dt[k * nb + r] = D[r, k]
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int r = e / nb, k = e % nb;
+    Dt[k * nb + r] = D[int64_t(r) * ldd + k];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = int64_t(blockIdx.x) * 8 + warp;
+  if (c >= ncols) return;
+  const V zero = {T(0), T(0)};
+  V x0 = lane < nb ? X[int64_t(lane) * ldx + c] : zero;
+  V x1 = lane + 32 < nb ? X[int64_t(lane + 32) * ldx + c] : zero;
+  auto bcast = [&](int i) {
+    V v = i < 32 ? x0 : x1;
+    v.x = __shfl_sync(0xffffffffu, v.x, i & 31);
+    v.y = __shfl_sync(0xffffffffu, v.y, i & 31);
+    return v;
+  };
+  auto fms = [](V a, V d, V x) {  // a - d x
+    a.x -= d.x * x.x - d.y * x.y;
+    a.y -= d.x * x.y + d.y * x.x;
+    return a;
+  };
+  if (!upper) {
+    for (int i = 0; i < nb - 1; ++i) {
+      V xi = bcast(i);
+      if (lane > i && lane < nb) x0 = fms(x0, Dt[i * nb + lane], xi);
+      if (lane + 32 > i && lane + 32 < nb) x1 = fms(x1, Dt[i * nb + lane + 32], xi);
+    }
+  } else {
+    for (int i = nb - 1; i >= 0; --i) {
+      V d = Dt[i * nb + i];
+      T den = d.x * d.x + d.y * d.y;
+      bool mine0 = i < 32 && lane == i, mine1 = i >= 32 && lane == i - 32;
+      if (mine0 || mine1) {
+        V v = mine0 ? x0 : x1;
+        V q = den > T(0) ? V{(v.x * d.x + v.y * d.y) / den, (v.y * d.x - v.x * d.y) / den} : zero;
+        if (mine0) x0 = q; else x1 = q;
+      }
+      V xi = bcast(i);
+      if (lane < i) x0 = fms(x0, Dt[i * nb + lane], xi);
+      if (lane + 32 < i) x1 = fms(x1, Dt[i * nb + lane + 32], xi);
+    }
+  }
+  if (lane < nb) X[int64_t(lane) * ldx + c] = x0;
+  if (lane + 32 < nb) X[int64_t(lane + 32) * ldx + c] = x1;
+}
+
 template <typename T>
 __global__ void gather_rows_kernel(const typename C2<T>::type* X, int64_t ldx, const int32_t* perm, int64_t n,
                                    int64_t nrhs, typename C2<T>::type* Y, int64_t ldy) {
@@ -529,12 +585,12 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
       default: FOSB_SKINNY(8); break;
     }
 #undef FOSB_SKINNY
-    return cudaGetLastError();
+    return launched();
   }
   if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
   dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
   gemm_tiled_kernel<T><<<grid, 256, 0, s>>>(opA, opB, M, N, K, T(alpha_re), T(alpha_im), a, lda, b, ldb, T(beta), c, ldc);
-  return cudaGetLastError();
+  return launched();
 }
 
 template cudaError_t gemm<double>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
@@ -585,9 +641,11 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
       break;
     }
     laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
+    note_launches(2);  // panel + row swaps
     int64_t rest = n - j0 - jb;
     if (rest > 0) {
       trsm_diag_kernel<T><<<cdiv(rest, 128), 128, 0, s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
+      note_launches(1);
       e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0, Ap + jb * lda + jb, lda, s);
       if (e != cudaSuccess) {
         st = cuda_fail(e, "getrf: trailing update");
@@ -616,10 +674,26 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   if (e != cudaSuccess) return e;
   gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
   const int nb = 64;
+  const bool warp_mode = nrhs <= 32;
+  static bool attr_set[2] = {false, false};
+  if (warp_mode && !attr_set[sizeof(T) == 8]) {
+    cudaFuncSetAttribute(trsv_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(nb * nb * sizeof(V)));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  auto diag = [&](int64_t i0, int ib, int upper) {
+    const V* D = LU + i0 * ldlu + i0;
+    if (warp_mode)
+      trsv_warp_kernel<T><<<cdiv(nrhs, 8), 256, size_t(ib) * ib * sizeof(V), s>>>(D, ldlu, ib, upper, tmp + i0 * nrhs,
+                                                                                 nrhs, nrhs);
+    else
+      trsm_diag_kernel<T><<<cdiv(nrhs, 128), 128, 0, s>>>(D, ldlu, ib, upper, tmp + i0 * nrhs, nrhs, nrhs);
+    note_launches(1);
+  };
+  note_launches(2);  // gather + final copy
   // forward: unit lower
   for (int64_t i0 = 0; i0 < n; i0 += nb) {
     int ib = int(std::min<int64_t>(nb, n - i0));
-    trsm_diag_kernel<T><<<cdiv(nrhs, 128), 128, 0, s>>>(LU + i0 * ldlu + i0, ldlu, ib, 0, tmp + i0 * nrhs, nrhs, nrhs);
+    diag(i0, ib, 0);
     int64_t rest = n - i0 - ib;
     if (rest > 0) {
       e = gemm<T>(OP_N, OP_N, rest, nrhs, ib, -1.0, 0.0, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0,
@@ -631,7 +705,7 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   for (int64_t i1 = n; i1 > 0; i1 -= nb) {
     int64_t i0 = std::max<int64_t>(0, i1 - nb);
     int ib = int(i1 - i0);
-    trsm_diag_kernel<T><<<cdiv(nrhs, 128), 128, 0, s>>>(LU + i0 * ldlu + i0, ldlu, ib, 1, tmp + i0 * nrhs, nrhs, nrhs);
+    diag(i0, ib, 1);
     if (i0 > 0) {
       e = gemm<T>(OP_N, OP_N, i0, nrhs, ib, -1.0, 0.0, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0, tmp, nrhs, s);
       if (e != cudaSuccess) return e;
@@ -650,14 +724,14 @@ cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int
   if (rows * cols == 0) return cudaSuccess;
   c128_to_c64_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const double2*>(src), rows, cols, lds,
                                                             static_cast<float2*>(dst), ldd);
-  return cudaGetLastError();
+  return launched();
 }
 cudaError_t convert_c64_to_c128(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                 cudaStream_t s) {
   if (rows * cols == 0) return cudaSuccess;
   c64_to_c128_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const float2*>(src), rows, cols, lds,
                                                             static_cast<double2*>(dst), ldd);
-  return cudaGetLastError();
+  return launched();
 }
 cudaError_t copy_matrix(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd, size_t elem,
                         cudaStream_t s) {
@@ -668,7 +742,7 @@ cudaError_t axpy_c64_into_c128(const void* d, int64_t rows, int64_t cols, int64_
   if (rows * cols == 0) return cudaSuccess;
   axpy_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const float2*>(d), rows, cols, ldd,
                                                      static_cast<double2*>(x), ldx);
-  return cudaGetLastError();
+  return launched();
 }
 cudaError_t add_mirrored(const void* M, int64_t n, int64_t ldm, int op, double w, bool accumulate, bool c64, void* out,
                          int64_t ldo, cudaStream_t s) {
@@ -679,21 +753,21 @@ cudaError_t add_mirrored(const void* M, int64_t n, int64_t ldm, int op, double w
   else
     add_mirrored_kernel<double><<<cdiv(n * n, 256), 256, 0, s>>>(static_cast<const double2*>(M), n, ldm, op, w,
                                                                  accumulate, static_cast<double2*>(out), ldo);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t norm_inf_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;
   row_norm_kernel<<<cdiv(rows, 8), 256, 0, s>>>(static_cast<const double2*>(A), rows, cols, lda, d_out);
-  return cudaGetLastError();
+  return launched();
 }
 cudaError_t absmax_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * cols, s);
   if (e != cudaSuccess) return e;
   if (rows * cols == 0) return cudaSuccess;
   col_absmax_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const double2*>(A), rows, cols, lda, d_out);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace fosb

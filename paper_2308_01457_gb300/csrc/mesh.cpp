@@ -2,6 +2,7 @@
 // (Section IV: lowest-order div-conforming elements on flat triangles) and the
 // touching-pair list for the singular quadrature.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -13,6 +14,9 @@
 namespace fosb {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -109,6 +113,8 @@ extern "C" {
 const char* fosb_last_error(void) { return g_last_error.c_str(); }
 
 const char* fosb_version(void) { return "fosb-gb300 0.1 (sm_103a)"; }
+
+uint64_t fosb_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 fosb_status fosb_mesh_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, const double* vnormals,
                              fosb_mesh* out) {

@@ -1,0 +1,155 @@
+"""Combination-technique driver of the FOSB second moment (Section IV-B) on one GPU.
+
+The index sets Lambda_+/- and the Hermitian reduction are host bookkeeping; every
+numerical step runs through the C ABI (assembly, factorisation, refined solves,
+covariance blocks, far-field moments).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (ASM_FP64, COV_GAUSS, FP32, MIXED, assemble_efie, covariance, factor, farfield_moments, incidence,
+               mesh_create, solve)
+
+
+def index_sets(L0: int, L: int):
+    """Lambda_+ = {(l1, l2): l1 + l2 = L + L0}, Lambda_- = {l1 + l2 = L + L0 - 1}, both
+    restricted to L0 <= l1, l2 <= L."""
+    plus = [(a, L + L0 - a) for a in range(L0, L + 1) if L0 <= L + L0 - a <= L]
+    minus = [(a, L + L0 - 1 - a) for a in range(L0, L + 1) if L0 <= L + L0 - 1 - a <= L]
+    return plus, minus
+
+
+def hermitian_blocks(L0: int, L: int):
+    """The blocks actually solved: l1 >= l2 on Lambda_+ (sign +1) and Lambda_- (sign -1);
+    Sigma_{l2,l1} = Sigma_{l1,l2}^H supplies the rest (Section IV-B)."""
+    plus, minus = index_sets(L0, L)
+    return [(b, 1) for b in plus if b[0] >= b[1]] + [(b, -1) for b in minus if b[0] >= b[1]]
+
+
+def dofs(n_of_level, L0: int, L: int):
+    """(N_hat_L, N_hat_L^max) of eq. efficiency for the full index set Lambda."""
+    plus, minus = index_sets(L0, L)
+    sizes = [n_of_level[a] * n_of_level[b] for a, b in plus + minus]
+    return sum(sizes), max(sizes)
+
+
+@dataclass
+class LevelState:
+    mesh: object
+    Z: object
+    b: object
+    u: object = None
+    lu: object = None
+    iters: int = 0
+    berr: float = 0.0
+
+
+@dataclass
+class FOSBProblem:
+    """One FOSB run: meshes of levels L0..L (meshes[i] is level L0 + i), wavenumber k,
+    one plane wave (d, p), observation directions, covariance kernel of the normal
+    perturbation."""
+
+    meshes: list
+    k: float
+    d: tuple
+    p: tuple
+    dirs: np.ndarray
+    L0: int
+    L: int
+    kernel: int = COV_GAUSS
+    sigma: float = 1.0
+    ell: float = 1.0
+    prec: int = MIXED
+    arith: int = ASM_FP64
+    n_ss: int = 5
+    pseudo: bool = False
+    levels: dict = field(default_factory=dict)
+
+    def setup(self, device="cuda:0"):
+        """fosb_mesh_create for every level and device buffers for Z and b (A1)."""
+        import torch
+
+        dt = torch.complex64 if self.prec == FP32 else torch.complex128
+        for i, sm in enumerate(self.meshes):
+            l = self.L0 + i
+            m = mesh_create(sm.verts, sm.tris, sm.vnormals)
+            N = m.n_edges
+            self.levels[l] = LevelState(m, torch.empty((N, N), dtype=dt, device=device),
+                                        torch.empty((N, 1), dtype=dt, device=device))
+        self.inc = incidence(self.d, self.p)
+        return self
+
+    def nominal(self, l: int, timers=None):
+        """A2-A6 for one level: assembly, factorisation, refined solve.  timers: optional
+        dict name -> list of (start, end) CUDA events recorded on the current stream."""
+        import torch
+
+        def ev(name):
+            if timers is None:
+                return None
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            timers.setdefault(f"{name}_l{l}", []).append((a, b))
+            a.record()
+            return b
+
+        st = self.levels[l]
+        e = ev("assemble")
+        assemble_efie(st.mesh, self.k, st.Z, inc=self.inc, b=st.b, n_ss=self.n_ss, arith=self.arith, prec=self.prec)
+        if e is not None:
+            e.record()
+        e = ev("factor")
+        st.lu = factor(st.Z, prec=self.prec)
+        if e is not None:
+            e.record()
+        if st.u is None:
+            st.u = torch.empty_like(st.b)
+        e = ev("solve")
+        _, st.iters, st.berr = solve(st.lu, st.b, st.u)
+        if e is not None:
+            e.record()
+        return st
+
+    def run(self, timers=None):
+        """Full step: nominal solves on all levels, the mean far field on level L, and the
+        CT far-field covariance (and pseudo-covariance if requested).  Returns device
+        tensors (F_mean (3 n_dir x 1), Cov (3 n_dir x 3 n_dir)[, PCov])."""
+        import torch
+
+        nd3 = 3 * self.dirs.shape[0]
+        dt = self.levels[self.L].Z.dtype
+        dev = self.levels[self.L].Z.device
+        for l in sorted(self.levels):
+            self.nominal(l, timers)
+        if timers is not None:
+            cov_start = torch.cuda.Event(enable_timing=True)
+            cov_start.record()
+        fine = self.levels[self.L]
+        F = torch.empty((nd3, 1), dtype=dt, device=dev)
+        farfield_moments(fine.mesh, self.k, self.dirs, fine.u, F)
+        cov = torch.empty((nd3, nd3), dtype=dt, device=dev)
+        pcov = torch.empty((nd3, nd3), dtype=dt, device=dev) if self.pseudo else None
+        first = True
+        for (l1, l2), sgn in hermitian_blocks(self.L0, self.L):
+            a, c = self.levels[l1], self.levels[l2]
+            for pseudo, out in ((False, cov), (True, pcov)):
+                if out is None:
+                    continue
+                Sig = torch.empty((a.mesh.n_edges, c.mesh.n_edges), dtype=dt, device=dev)
+                covariance(a.mesh, a.lu, a.u, c.mesh, c.lu, c.u, self.k, Sig, self.kernel, self.sigma, self.ell,
+                           pseudo=pseudo)
+                farfield_moments(a.mesh, self.k, self.dirs, Sig, out, m2=c.mesh, weight=float(sgn), mirror=(l1 != l2),
+                                 pseudo=pseudo, accumulate=not first)
+            first = False
+        if timers is not None:
+            cov_end = torch.cuda.Event(enable_timing=True)
+            cov_end.record()
+            timers.setdefault("covariance_ct", []).append((cov_start, cov_end))
+        return (F, cov) if pcov is None else (F, cov, pcov)
+
+    def release(self):
+        for st in self.levels.values():
+            st.lu = None
