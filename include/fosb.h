@@ -175,6 +175,24 @@ fosb_status fosb_solve(fosb_lu lu, char op, const void* B, int64_t nrhs, int64_t
 fosb_status fosb_lu_info(fosb_lu lu, int64_t* n, int* prec, double* znorm_inf);
 fosb_status fosb_lu_destroy(fosb_lu lu);
 
+/* ---- In-place LU that allocates no device memory -----------------------------------
+ * The paper has no counterpart: this is a library-integration entry point.  For callers
+ * that cannot call cudaMalloc/cudaFree while they use the library (hosts whose own
+ * allocator owns all device memory, or that forbid allocation after start-up because it
+ * can synchronise the device), it factors the caller's matrix in place, P A = L U with
+ * the same partial pivoting and kernels as fosb_factor, and allocates nothing: the panel
+ * kernel's scratch lives in a 1 MiB static device array that every GPU loading the
+ * library holds until the process exits.
+ *   A    : device, n x n row-major (lda >= n), complex128 (prec = FOSB_FP64) or complex64
+ *          (prec = FOSB_FP32); overwritten by L (unit lower, below the diagonal) and U.
+ *   ipiv : device, n int32: at step i row i was interchanged with row ipiv[i] (0-based).
+ * Limits: n <= 524288 (256 panel CTAs of at most 2048 rows); larger n -> FOSB_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Calls share
+ * the array: calls that overlap on the GPU race.  Synchronises `stream` to read the
+ * status word.  Errors: FOSB_ERR_SINGULAR, FOSB_ERR_TIMEOUT, FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_getrf_static(void* A, int64_t n, int64_t lda, int prec, int32_t* ipiv, void* stream);
+
 /* ---- A7-A9: shape-derivative covariance of one combination-technique block --------
  * Sigma solves (Z_1 (x) conj Z_2) Sigma = C (eq. CTsubsystem), i.e. Z_1 Sigma Z_2^H = C,
  * with C = B_1 K_12 B_2^H = E[g_1 g_2^H]:

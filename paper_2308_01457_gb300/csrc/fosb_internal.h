@@ -125,6 +125,10 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
                  int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s);
 template <typename T>
 fosb_status getrf(void* A, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, cudaStream_t s);
+size_t getrf_scratch_bytes(int64_t max_ctas, bool c128);
+template <typename T>
+fosb_status getrf_external_scratch(void* A, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, void* scratch,
+                                   int64_t max_ctas, cudaStream_t s);
 template <typename T>
 cudaError_t getrs(const void* LU, int64_t n, int64_t ldlu, const int32_t* ipiv, void* X, int64_t nrhs, int64_t ldx,
                   cudaStream_t s);

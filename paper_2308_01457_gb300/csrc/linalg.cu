@@ -662,6 +662,62 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
 template fosb_status getrf<double>(void*, int64_t, int64_t, int32_t*, int*, cudaStream_t);
 template fosb_status getrf<float>(void*, int64_t, int64_t, int32_t*, int*, cudaStream_t);
 
+size_t getrf_scratch_bytes(int64_t max_ctas, bool c128) {
+  const size_t v = c128 ? 16 : 8, nb = 64;
+  return 256 + 2 * size_t(max_ctas) * (sizeof(double) + sizeof(int64_t)) + 2 * size_t(max_ctas) * nb * v + 2 * nb * v;
+}
+
+// The same blocked factorisation as getrf, with the panel kernel's scratch (barrier
+// words and pivot candidates, getrf_scratch_bytes(max_ctas)) supplied by the caller;
+// allocates nothing.  The first 256 bytes of `scratch` must be zero on entry.
+template <typename T>
+fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, void* scratch,
+                                   int64_t max_ctas, cudaStream_t s) {
+  using V = typename C2<T>::type;
+  V* A = static_cast<V*>(Av);
+  const int nb = 64;
+  int dev = 0, nsm = 0, per_sm = 0;
+  FOSB_CUDA(cudaGetDevice(&dev));
+  FOSB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  FOSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<T>, kPanelThreads, 0));
+  if (per_sm < 1) return fail(FOSB_ERR_CUDA, "getrf: panel kernel cannot be resident");
+  const int64_t G_cap = std::min<int64_t>(int64_t(nsm) * per_sm, max_ctas);
+  char* base = static_cast<char*>(scratch);
+  PanelScratch* scr = reinterpret_cast<PanelScratch*>(base);
+  double* cand_val = reinterpret_cast<double*>(base + 256);
+  int64_t* cand_row = reinterpret_cast<int64_t*>(cand_val + 2 * max_ctas);
+  V* cand_data = reinterpret_cast<V*>(cand_row + 2 * max_ctas);
+  V* rowj = cand_data + 2 * max_ctas * nb;
+  for (int64_t j0 = 0; j0 < n; j0 += nb) {
+    int jb = int(std::min<int64_t>(nb, n - j0));
+    int64_t m = n - j0;
+    int64_t G = std::min<int64_t>(G_cap, std::max<int64_t>(1, (m + 63) / 64));
+    if ((m + G - 1) / G > kMaxPanelRows) return fail(FOSB_ERR_INVALID_ARG, "getrf: matrix too large for the panel kernel");
+    V* Ap = A + j0 * lda + j0;
+    int32_t* ip = ipiv + j0;
+    int64_t row_base = j0;
+    void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
+    FOSB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)),
+                                          dim3(kPanelThreads), args, 0, s));
+    laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
+    note_launches(2);
+    int64_t rest = n - j0 - jb;
+    if (rest > 0) {
+      trsm_diag_kernel<T><<<cdiv(rest, 128), 128, 0, s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
+      note_launches(1);
+      FOSB_CUDA(gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0,
+                        Ap + jb * lda + jb, lda, s));
+    }
+    FOSB_CUDA(cudaGetLastError());
+  }
+  return FOSB_OK;
+}
+
+template fosb_status getrf_external_scratch<double>(void*, int64_t, int64_t, int32_t*, int*, void*, int64_t,
+                                                    cudaStream_t);
+template fosb_status getrf_external_scratch<float>(void*, int64_t, int64_t, int32_t*, int*, void*, int64_t,
+                                                   cudaStream_t);
+
 // X <- Z^{-1} X given the factors (perm = composed row permutation, device).
 template <typename T>
 cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm, void* Xv, int64_t nrhs, int64_t ldx,
