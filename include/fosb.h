@@ -82,7 +82,9 @@ typedef struct {
 
 typedef struct {
   int max_iters;     /* iterative-refinement steps (default 10) */
-  double tol;        /* stop when ||b - Z x||_inf / (||Z||_inf ||x||_inf + ||b||_inf) <= tol (default 64 * 2^-52) */
+  double tol;        /* stop when ||b - Z x||_inf / (||Z||_inf ||x||_inf + ||b||_inf) <= tol per column;
+                        tol <= 0 selects the default max(64, 8 sqrt(n)) * 2^-52.  Refinement also stops
+                        when a step gains less than a factor 2 below 1e-13 (rounding floor reached) */
 } fosb_refine_opts;
 
 typedef struct {
@@ -230,6 +232,26 @@ fosb_status fosb_covariance(fosb_mesh m1, fosb_lu lu1, const void* u1, fosb_mesh
 fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const double* dirs, int64_t n_dir,
                                   const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
                                   int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream);
+
+/* ---- A12: monostatic RCS and its adjoint shape gradient --------------------------
+ * For n plane waves E_inc_i = p_i exp(ik d_i . x) with solved currents U (u_i = Z^{-1} b_i),
+ * the monostatic far field F_i = F(xh_i), xh_i = -d_i (Section II-C expansion), and
+ *     sigma_i = |F_i|^2 / (4 pi)            (eq. RCS read with that expansion: RCS_dB = 10 log10 sigma).
+ * With grad != NULL the call also writes grad = sum_i weights_i d sigma_i / dX (V x 3, the
+ * exact derivative of the discrete sigma with respect to every vertex coordinate):
+ *     d sigma_i = (2/(4 pi)) Re[conj(F_i) . (dA_i u_i + A_i Z^{-1}(db_i - dZ u_i))],
+ * evaluated by the adjoint lambda_i = Z^{-1} A_i^T c_i (Z^T = Z) and reverse-mode kernels
+ * over the same triangle pairs and quadrature points as the assembly.  The paper
+ * differentiates the continuous problem (Section III); this is the discrete counterpart.
+ *   lu      : factorisation of Z (FOSB_FP64 or FOSB_MIXED); needed only with grad
+ *   inc     : host, n x 9 (d, Re p, Im p) as in fosb_assemble_efie
+ *   U       : device, N x n complex128 (ldu >= n)
+ *   weights : host, n (dL/dsigma_i); needed only with grad
+ *   sigma   : host, n outputs (may be NULL);  grad : device, V x 3 float64 (overwritten) or NULL
+ * Synchronises `stream`. */
+fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb_quad_opts* opts, const double* inc,
+                                int64_t n_inc, const void* U, int64_t ldu, const double* weights, double* sigma,
+                                double* grad, void* stream);
 
 #ifdef __cplusplus
 }

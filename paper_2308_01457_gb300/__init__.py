@@ -66,7 +66,8 @@ def lib():
         L.fosb_kernel_launches.restype = ctypes.c_uint64
         for name in ("fosb_mesh_create", "fosb_mesh_info", "fosb_mesh_edges", "fosb_mesh_destroy",
                      "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
-                     "fosb_covariance", "fosb_farfield_moments"):
+                     "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
+                     "fosb_getrf_static"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -180,7 +181,7 @@ def factor(Z, prec: int | None = None, stream=None) -> LU:
     return LU(h, Z.shape[0], prec, Z)
 
 
-def solve(lu: LU, B, X=None, max_iters: int = 10, tol: float = 64 * 2.0**-52, stream=None):
+def solve(lu: LU, B, X=None, max_iters: int = 10, tol: float = 0.0, stream=None):
     """fosb_solve: X = Z^{-1} B (in place when X is None).  Returns (X, iters, backward_error)."""
     X = B if X is None else X
     nrhs = 1 if B.dim() == 1 else B.shape[1]
@@ -194,7 +195,7 @@ def solve(lu: LU, B, X=None, max_iters: int = 10, tol: float = 64 * 2.0**-52, st
 
 def covariance(m1: Mesh, lu1: LU, u1, m2: Mesh, lu2: LU, u2, k: float, Sigma, kind: int = COV_GAUSS,
                sigma: float = 1.0, ell: float = 1.0, pseudo: bool = False, max_iters: int = 10,
-               tol: float = 64 * 2.0**-52, stream=None):
+               tol: float = 0.0, stream=None):
     """fosb_covariance: Sigma (N1 x N2) with Z1 Sigma Z2^H = B1 K12 B2^H (or the pseudo form)."""
     ker = CovKernel(kind, sigma, ell)
     ro = RefineOpts(max_iters, tol)
@@ -219,3 +220,21 @@ def farfield_moments(m1: Mesh, k: float, dirs, X, out, m2: Mesh | None = None, w
                                        ctypes.c_int(prec), _ptr(out), ctypes.c_int64(1 if out.dim() == 1 else _ld(out)),
                                        ctypes.c_int(int(accumulate)), _stream(stream)))
     return out
+
+
+def rcs_monostatic(mesh: Mesh, k: float, inc, U, lu: LU | None = None, weights=None, grad=None, n_ss: int = 5,
+                   stream=None):
+    """fosb_rcs_monostatic: sigma_i = |F(-d_i)|^2/(4 pi) (numpy, n) for solved currents U
+    (N x n); with `grad` (device V x 3 float64) also sum_i weights_i d sigma_i / dX."""
+    inc_a = _np(inc, np.float64).reshape(-1, 9)
+    n = inc_a.shape[0]
+    sig = np.zeros(n)
+    w = None if weights is None else _np(weights, np.float64)
+    opts = QuadOpts(n_ss, ASM_FP64)
+    _check(lib().fosb_rcs_monostatic(mesh.handle, None if lu is None else lu.handle, ctypes.c_double(k),
+                                     ctypes.byref(opts), inc_a.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n),
+                                     _ptr(U), ctypes.c_int64(_ld(U)),
+                                     None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                                     sig.ctypes.data_as(ctypes.c_void_p), None if grad is None else _ptr(grad),
+                                     _stream(stream)))
+    return sig

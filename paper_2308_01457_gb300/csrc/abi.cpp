@@ -34,7 +34,9 @@ fosb_status ensure_rules(int nss) {
   FOSB_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(FOSB_ERR_INVALID_ARG, "device index out of range");
   if (g_rules_nss[dev] != nss) {
-    upload_rules(make_rules(nss));
+    Rules r = make_rules(nss);
+    upload_rules(r);
+    upload_rules_adjoint(r);
     FOSB_CUDA(cudaDeviceSynchronize());
     g_rules_nss[dev] = nss;
   }
@@ -79,7 +81,9 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   }
   // MIXED: complex64 factors, FP64 residuals.
   const int max_iters = ropt ? ropt->max_iters : 10;
-  const double tol = ropt ? ropt->tol : 64.0 * std::ldexp(1.0, -52);
+  // default: the FP64 residual floor grows like sqrt(n) eps; stop at 8 sqrt(n) eps (>= 64 eps)
+  const double eps = std::ldexp(1.0, -52);
+  const double tol = (ropt && ropt->tol > 0) ? ropt->tol : std::max(64.0, 8.0 * std::sqrt(double(n))) * eps;
   Scratch r(s), d(s), bkeep(s), nb(s);
   FOSB_CUDA(r.alloc(sizeof(double) * 2 * n * nrhs));
   FOSB_CUDA(d.alloc(sizeof(float) * 2 * n * nrhs));
@@ -112,6 +116,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
     }
     if (berr <= tol || it >= max_iters) break;
     if (berr >= prev && prev >= prev2) break;  // no decrease over two steps
+    if (berr < 1e-13 && berr > 0.5 * prev) break;  // at the rounding floor: progress has stalled
     prev2 = prev;
     prev = berr;
     FOSB_CUDA(convert_c128_to_c64(r.p, n, nrhs, nrhs, d.p, nrhs, s));
@@ -349,6 +354,104 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
   return FOSB_OK;
 }
 
-}  // extern "C"
+fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb_quad_opts* opts, const double* inc,
+                                int64_t n_inc, const void* U, int64_t ldu, const double* weights, double* sigma,
+                                double* grad, void* stream) {
+  if (!mesh || !inc || !U || n_inc <= 0 || ldu < n_inc) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: bad arguments");
+  if (!(k > 0)) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: k must be > 0");
+  if (grad && (!lu || !weights)) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: gradient needs lu and weights");
+  if (lu && (lu->prec == FOSB_FP32 || lu->n != mesh->d.ne))
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: lu must be an FP64 or MIXED factorisation of this mesh");
+  const int nss = opts && opts->n_ss > 0 ? opts->n_ss : 5;
+  if (nss > 12) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: n_ss must be in 1..12");
+  FOSB_TRY(ensure_rules(nss));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const DevMesh& d = mesh->d;
+  const int64_t N = d.ne, n = n_inc, nd3 = 3 * n_inc;
+  // observation directions of the monostatic set: xh_i = -d_i
+  std::vector<double> xh(3 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) xh[3 * i + c] = -inc[9 * i + c];
+  Scratch dxh(s), A(s), FA(s);
+  FOSB_CUDA(dxh.alloc(sizeof(double) * 3 * n));
+  FOSB_CUDA(cudaMemcpyAsync(dxh.p, xh.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+  FOSB_CUDA(A.alloc(16 * nd3 * N));
+  FOSB_CUDA(cudaMemsetAsync(A.p, 0, 16 * nd3 * N, s));
+  FOSB_CUDA(launch_farfield_matrix(d, k, dxh.as<double>(), n, false, A.p, s));
+  FOSB_CUDA(FA.alloc(16 * nd3 * n));
+  FOSB_CUDA(gemm<double>(OP_N, OP_N, nd3, n, N, 1.0, 0.0, A.p, N, U, ldu, 0.0, FA.p, n, s));
+  std::vector<double> fa(2 * nd3 * n);
+  FOSB_CUDA(cudaMemcpyAsync(fa.data(), FA.p, 16 * nd3 * n, cudaMemcpyDeviceToHost, s));
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  // F_i = (A u_i) at xh_i: rows 3i..3i+2 of column i;  sigma_i = |F_i|^2 / (4 pi)
+  std::vector<double> sig(n), Fr(3 * n), Fi(3 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    double s2 = 0;
+    for (int c = 0; c < 3; ++c) {
+      Fr[3 * i + c] = fa[2 * ((3 * i + c) * n + i)];
+      Fi[3 * i + c] = fa[2 * ((3 * i + c) * n + i) + 1];
+      s2 += Fr[3 * i + c] * Fr[3 * i + c] + Fi[3 * i + c] * Fi[3 * i + c];
+    }
+    sig[i] = s2 / (4.0 * M_PI);
+  }
+  if (sigma) std::memcpy(sigma, sig.data(), sizeof(double) * n);
+  if (!grad) return FOSB_OK;
+  // Adjoint: dsigma_i = (2/(4 pi)) Re[conj(F_i).(dA_i u_i + A_i du_i)], du_i = Z^{-1}(db_i - dZ u_i);
+  // with c_i = w_i (2/(4 pi)) conj(F_i) and lambda_i = Z^{-1} A_i^T c_i (Z^T = Z):
+  //   sum_i w_i dsigma_i = Re[sum_i c_i.dA_i u_i + lambda_i^T db_i - lambda_i^T dZ u_i].
+  std::vector<double> Cm(2 * nd3 * n, 0.0), pw(11 * 2 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    double sc = weights[i] * 2.0 / (4.0 * M_PI);
+    double cr[3], ci[3];
+    for (int c = 0; c < 3; ++c) {
+      cr[c] = sc * Fr[3 * i + c];
+      ci[c] = -sc * Fi[3 * i + c];
+      Cm[2 * ((3 * i + c) * n + i)] = cr[c];
+      Cm[2 * ((3 * i + c) * n + i) + 1] = ci[c];
+    }
+    // b-part: d_i, pi = p_i, alpha = -1 (weights lambda); A-part: -xh_i = d_i,
+    // pi = (I - xh xh^T) c_i, alpha = -ik (weights U)
+    double* pb = &pw[11 * i];
+    double* pa = &pw[11 * (n + i)];
+    const double* row = inc + 9 * i;
+    for (int c = 0; c < 3; ++c) {
+      pb[c] = row[c];
+      pb[3 + c] = row[3 + c];
+      pb[6 + c] = row[6 + c];
+      pa[c] = row[c];
+    }
+    pb[9] = -1.0;
+    pb[10] = 0.0;
+    double xr = xh[3 * i] * cr[0] + xh[3 * i + 1] * cr[1] + xh[3 * i + 2] * cr[2];
+    double xi = xh[3 * i] * ci[0] + xh[3 * i + 1] * ci[1] + xh[3 * i + 2] * ci[2];
+    for (int c = 0; c < 3; ++c) {
+      pa[3 + c] = cr[c] - xh[3 * i + c] * xr;
+      pa[6 + c] = ci[c] - xh[3 * i + c] * xi;
+    }
+    pa[9] = 0.0;
+    pa[10] = -k;
+  }
+  Scratch dC(s), lam(s), dpw(s);
+  FOSB_CUDA(dC.alloc(16 * nd3 * n));
+  FOSB_CUDA(cudaMemcpyAsync(dC.p, Cm.data(), 16 * nd3 * n, cudaMemcpyHostToDevice, s));
+  FOSB_CUDA(lam.alloc(16 * N * n));
+  FOSB_CUDA(gemm<double>(OP_T, OP_N, N, n, nd3, 1.0, 0.0, A.p, N, dC.p, n, 0.0, lam.p, n, s));
+  FOSB_TRY(solve_internal(lu, lam.p, n, n, lam.p, n, nullptr, nullptr, s));
+  FOSB_CUDA(dpw.alloc(sizeof(double) * 11 * 2 * n));
+  FOSB_CUDA(cudaMemcpyAsync(dpw.p, pw.data(), sizeof(double) * 11 * 2 * n, cudaMemcpyHostToDevice, s));
+  FOSB_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * d.nv, s));
+  const double* Uc = static_cast<const double*>(U);
+  Scratch ucopy(s);
+  if (ldu != n) {  // the pair kernel reads lambda and U with one leading dimension
+    FOSB_CUDA(ucopy.alloc(16 * N * n));
+    FOSB_CUDA(copy_matrix(U, N, n, ldu, ucopy.p, n, 16, s));
+    Uc = ucopy.as<double>();
+  }
+  FOSB_CUDA(launch_adjoint_pairs(d, k, nss, lam.as<double>(), Uc, n, n, grad, s));
+  FOSB_CUDA(launch_adjoint_planewave(d, k, n, dpw.as<double>(), lam.as<double>(), n, grad, s));
+  FOSB_CUDA(launch_adjoint_planewave(d, k, n, dpw.as<double>() + 11 * n, static_cast<const double*>(U), ldu, grad, s));
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  return FOSB_OK;
+}
 
-// Float-float regular assembly: provided by ff_assemble.cu.
+}  // extern "C"

@@ -104,6 +104,14 @@ cudaError_t launch_assemble_singular(const DevMesh& m, double k, int nss, bool f
 cudaError_t launch_rhs(const DevMesh& m, double k, const double* d_inc, int64_t n_inc, bool fp32_out, void* b,
                        int64_t ldb, cudaStream_t s);
 void upload_rules(const Rules& r);
+void upload_rules_adjoint(const Rules& r);
+// Adjoint shape gradients (see adjoint.cu): grad (V x 3) += -grad Re sum_i lam_i^T Z u_i, and
+// += grad Re J_P for plane-wave moments with per-column parameters d_pw (ncols x 11:
+// d(3), Re pi(3), Im pi(3), alpha (re, im)) and edge weights wgt (N x ncols, ldw).
+cudaError_t launch_adjoint_pairs(const DevMesh& m, double k, int nss, const double* lam, const double* U, int64_t ld,
+                                 int64_t nrhs, double* grad, cudaStream_t s);
+cudaError_t launch_adjoint_planewave(const DevMesh& m, double k, int64_t ncols, const double* d_pw, const double* wgt,
+                                     int64_t ldw, double* grad, cudaStream_t s);
 cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_t ldz, cudaStream_t s);
 
 // Far field

@@ -134,6 +134,108 @@ __global__ void __launch_bounds__(256) gemm_tiled_kernel(int opA, int opB, int64
   }
 }
 
+// ------------------------------------------------------------------ FP64 GEMM on DMMA
+// Complex128 C = alpha op(A) op(B) + beta C with mma.sync.m8n8k4 f64 (the FP64 tensor
+// path): each complex product is four real MMAs (Ar Br, -Ai Bi into the real part,
+// Ar Bi, Ai Br into the imaginary part).  CTA tile 64 x 64 (complex), k-tile 16, eight
+// warps in a 2 x 4 grid, 32 x 16 per warp (4 x 2 fragments of 8 x 8).  Fragment layout
+// of m8n8k4: A[g][t], B[t][g], C[g][2t + i] with g = lane / 4, t = lane % 4.
+constexpr int DBM = 64, DBN = 64, DBK = 16, DPA = 4, DPB = 2;
+
+__device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+               : "+d"(c0), "+d"(c1)
+               : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, double ar,
+                                                         double ai, const double2* __restrict__ A, int64_t lda,
+                                                         const double2* __restrict__ B, int64_t ldb, double beta,
+                                                         double2* __restrict__ C, int64_t ldc) {
+  __shared__ double2 As[DBM][DBK + DPA];
+  __shared__ double2 Bs[DBK][DBN + DPB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3;  // warp tile origin (wm * 32, wn * 16)
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t row0 = int64_t(blockIdx.y) * DBM, col0 = int64_t(blockIdx.x) * DBN;
+  double cr[4][2][2], ci[4][2][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) cr[i][j][e] = ci[i][j][e] = 0.0;
+  for (int64_t k0 = 0; k0 < K; k0 += DBK) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {  // A tile 64 x 16
+      int e = tid + 256 * l;
+      int r, kk;
+      if (opA == OP_N) {
+        r = e / DBK;
+        kk = e % DBK;
+      } else {
+        kk = e / DBM;
+        r = e % DBM;
+      }
+      int64_t gr = row0 + r, gk = k0 + kk;
+      As[r][kk] = (gr < M && gk < K) ? load_op<double>(A, gr, gk, lda, opA) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {  // B tile 16 x 64
+      int e = tid + 256 * l;
+      int c, kk;
+      if (opB == OP_N) {
+        kk = e / DBN;
+        c = e % DBN;
+      } else {
+        c = e / DBK;
+        kk = e % DBK;
+      }
+      int64_t gc = col0 + c, gk = k0 + kk;
+      Bs[kk][c] = (gc < N && gk < K) ? load_op<double>(B, gk, gc, ldb, opB) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < DBK; ks += 4) {
+      double2 a[4], b[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[wm * 32 + i * 8 + g][ks + t];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) b[j] = Bs[ks + t][wn * 16 + j * 8 + g];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          dmma(cr[i][j][0], cr[i][j][1], a[i].x, b[j].x);
+          dmma(cr[i][j][0], cr[i][j][1], -a[i].y, b[j].y);
+          dmma(ci[i][j][0], ci[i][j][1], a[i].x, b[j].y);
+          dmma(ci[i][j][0], ci[i][j][1], a[i].y, b[j].x);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t r = row0 + wm * 32 + i * 8 + g;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        int64_t c = col0 + wn * 16 + j * 8 + 2 * t + e;
+        if (c >= N) continue;
+        double xr = cr[i][j][e], xi = ci[i][j][e];
+        double2 v = make_double2(ar * xr - ai * xi, ar * xi + ai * xr);
+        if (beta != 0.0) {
+          double2 o = C[r * ldc + c];
+          v.x += beta * o.x;
+          v.y += beta * o.y;
+        }
+        C[r * ldc + c] = v;
+      }
+  }
+}
+
 // ------------------------------------------------------------------ skinny GEMM (op(A) = A)
 // One warp per row of A; lanes stride over K; N <= 8 columns of op(B).
 template <typename T, int NC>
@@ -471,6 +573,19 @@ __global__ void __launch_bounds__(256) trsv_warp_kernel(const typename C2<T>::ty
   if (lane + 32 < nb) X[int64_t(lane + 32) * ldx + c] = x1;
 }
 
+// Opt the warp-per-column solve into 64 KB of dynamic shared memory (a 64 x 64 complex128 block).
+template <typename T>
+void enable_trsv_smem() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !done[dev]) {
+    cudaFuncSetAttribute(trsv_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(64 * 64 * sizeof(typename C2<T>::type)));
+    done[dev] = true;
+  }
+}
+
 template <typename T>
 __global__ void gather_rows_kernel(const typename C2<T>::type* X, int64_t ldx, const int32_t* perm, int64_t n,
                                    int64_t nrhs, typename C2<T>::type* Y, int64_t ldy) {
@@ -588,6 +703,11 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
     return launched();
   }
   if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 8) {
+    dim3 gridd(cdiv(N, DBN), cdiv(M, DBM));
+    zgemm_dmma_kernel<<<gridd, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c, ldc);
+    return launched();
+  }
   dim3 grid(cdiv(N, TBN), cdiv(M, TBM));
   gemm_tiled_kernel<T><<<grid, 256, 0, s>>>(opA, opB, M, N, K, T(alpha_re), T(alpha_im), a, lda, b, ldb, T(beta), c, ldc);
   return launched();
@@ -644,7 +764,8 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
     note_launches(2);  // panel + row swaps
     int64_t rest = n - j0 - jb;
     if (rest > 0) {
-      trsm_diag_kernel<T><<<cdiv(rest, 128), 128, 0, s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
+      enable_trsv_smem<T>();
+      trsv_warp_kernel<T><<<cdiv(rest, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
       note_launches(1);
       e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0, Ap + jb * lda + jb, lda, s);
       if (e != cudaSuccess) {
@@ -703,7 +824,8 @@ fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ip
     note_launches(2);
     int64_t rest = n - j0 - jb;
     if (rest > 0) {
-      trsm_diag_kernel<T><<<cdiv(rest, 128), 128, 0, s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
+      enable_trsv_smem<T>();
+      trsv_warp_kernel<T><<<cdiv(rest, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
       note_launches(1);
       FOSB_CUDA(gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0,
                         Ap + jb * lda + jb, lda, s));
@@ -730,19 +852,11 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   if (e != cudaSuccess) return e;
   gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
   const int nb = 64;
-  const bool warp_mode = nrhs <= 32;
-  static bool attr_set[2] = {false, false};
-  if (warp_mode && !attr_set[sizeof(T) == 8]) {
-    cudaFuncSetAttribute(trsv_warp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(nb * nb * sizeof(V)));
-    attr_set[sizeof(T) == 8] = true;
-  }
+  enable_trsv_smem<T>();
   auto diag = [&](int64_t i0, int ib, int upper) {
     const V* D = LU + i0 * ldlu + i0;
-    if (warp_mode)
-      trsv_warp_kernel<T><<<cdiv(nrhs, 8), 256, size_t(ib) * ib * sizeof(V), s>>>(D, ldlu, ib, upper, tmp + i0 * nrhs,
-                                                                                 nrhs, nrhs);
-    else
-      trsm_diag_kernel<T><<<cdiv(nrhs, 128), 128, 0, s>>>(D, ldlu, ib, upper, tmp + i0 * nrhs, nrhs, nrhs);
+    trsv_warp_kernel<T><<<cdiv(nrhs, 8), 256, size_t(ib) * ib * sizeof(V), s>>>(D, ldlu, ib, upper, tmp + i0 * nrhs,
+                                                                               nrhs, nrhs);
     note_launches(1);
   };
   note_launches(2);  // gather + final copy
