@@ -340,7 +340,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fosb", choices=["fosb", "reference"])
     ap.add_argument("--workload", default="sphere-ka4-ct-L4", choices=sorted(WORKLOADS))
-    ap.add_argument("--arith", default="fp64", choices=["fp64", "ff"])
+    ap.add_argument("--arith", default="ff", choices=["fp64", "ff"],
+                    help="regular-pair assembly arithmetic: float-float on the FP32 pipe (default) or FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

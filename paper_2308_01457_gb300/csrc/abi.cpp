@@ -37,6 +37,7 @@ fosb_status ensure_rules(int nss) {
     Rules r = make_rules(nss);
     upload_rules(r);
     upload_rules_adjoint(r);
+    upload_rules_ff(r);
     FOSB_CUDA(cudaDeviceSynchronize());
     g_rules_nss[dev] = nss;
   }
@@ -154,6 +155,10 @@ fosb_status fosb_assemble_efie(fosb_mesh mesh, double k, const fosb_quad_opts* o
   if (is_c64(prec)) arith = FOSB_ASM_FP32;
   else if (arith == FOSB_ASM_FP32)
     return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: FP32 regular pairs need prec = FOSB_FP32");
+  if (arith == FOSB_ASM_FF && k * mesh->d.diameter >= ff_max_phase())
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: k * mesh diameter = " + std::to_string(k * mesh->d.diameter) +
+                                          " exceeds the float-float phase range " + std::to_string(ff_max_phase()) +
+                                          "; use FOSB_ASM_FP64");
   for (int64_t s = 0; s < n_inc; ++s)
     for (int c = 0; c < 9; ++c)
       if (!std::isfinite(inc[9 * s + c])) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_efie: non-finite incidence");

@@ -1,8 +1,345 @@
-// Float-float regular-pair assembly (placeholder until the FP32-pipe kernel lands).
+// Regular-pair EFIE assembly in float-float arithmetic on the FP32 pipe.
+//
+// GB300 issues FP64 at about 1/70 of its FP32 rate, so the FP64 kernel of assemble.cu is
+// bound by the FP64 pipe.  Here every quantity of the point-pair loop is an unevaluated
+// sum hi + lo of two floats (about 48 significant bits) built from error-free
+// transformations (two-sum, FMA two-product); no FP64 instruction remains in the loop.
+//
+// Per point pair (x_p on the test triangle, y_q on the trial triangle):
+//   d = (o1 - o2) + (x_p - o1) - (y_q - o2);  r = |d| (rsqrt seed + one Newton step);
+//   1/r (Newton step on the seed); theta = k r;
+//   exp(i theta): theta = j pi/64 + delta (Cody-Waite with a 3-part pi/64, j < 1024),
+//   sin/cos(delta) by Taylor series to delta^7 (|delta| <= pi/128) in float-float for
+//   the leading terms, combined with a 128-entry table of sin/cos(j pi/64);
+//   G0 = exp(i theta)/r.
+// The pair's 3 x 3 barycentric moment matrix
+//   mu_ab = sum_pq w_p w_q lambda_pa beta_qb G0(x_p, y_q)
+// determines the RWG block exactly (with P_a, Q_b the vertices):
+//   Z_ij = (s_i l_i s'_j l'_j / (4 pi)) [ -(ik/4) sum_ab mu_ab (P_a - P_i).(Q_b - Q_j) + (i/k) sum_ab mu_ab ],
+// which is formed in float-float and added to the complex128 Z with FP64 atomics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
 #include "fosb_internal.h"
 
 namespace fosb {
-cudaError_t launch_efie_regular_ff(const DevMesh&, double, double*, int64_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+struct ff {
+  float h, l;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
 }
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {  // accurate
+  ff s = two_sum(a.h, b.h);
+  ff t = two_sum(a.l, b.l);
+  s.l += t.h;
+  s = fast_two_sum(s.h, s.l);
+  s.l += t.l;
+  return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ ff ff_add_fast(ff a, ff b) {  // sloppy: fine without cancellation
+  ff s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  float p = a.h * b;
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqr(ff a) {
+  float p = a.h * a.h;
+  float e = fmaf(a.h, a.h, -p);
+  e = fmaf(2.0f * a.h, a.l, e);
+  return fast_two_sum(p, e);
+}
+// acc += a * c (compensated; acc is renormalised by the caller when read)
+__device__ __forceinline__ void acc_mul(ff& acc, ff a, ff c) {
+  float p = a.h * c.h;
+  float pe = fmaf(a.h, c.h, -p);
+  pe = fmaf(a.h, c.l, fmaf(a.l, c.h, pe));
+  float s = acc.h + p;
+  float bb = s - acc.h;
+  float e = (acc.h - (s - bb)) + (p - bb);
+  acc.h = s;
+  acc.l += e + pe;
+}
+__device__ __forceinline__ ff norm(ff a) { return fast_two_sum(a.h, a.l); }
+__device__ __forceinline__ double to_d(ff a) { return double(a.h) + double(a.l); }
+
+struct CFF {
+  ff r, i;
+};
+
+// constants: sin / cos (j pi / 64), j = 0..127, as (S.h, S.l, C.h, C.l); w_q beta_qb as ff
+__constant__ float c_sctab[128][4];
+__constant__ float c_wb[6][3][2];
+
+struct FFConst {
+  ff k, k4, kinv, inv4pi, sixth;
+  float c1, c2, c3, inv_c;  // pi/64 = c1 + c2 + c3 (c1, c2 with <= 14 significant bits); 64/pi
+};
+
+__device__ __forceinline__ ff ldff(const float* base, int64_t nt, int f, int64_t t) {
+  return {base[int64_t(f) * nt + t], base[int64_t(f + 1) * nt + t]};
+}
+
+// exp(i theta) for theta = th + tl >= 0, |j| < 1024, table in shared memory
+__device__ __forceinline__ void expi_ff(ff theta, const FFConst& C, const float (*tab)[4], ff& cs, ff& sn) {
+  const float jf = rintf(theta.h * C.inv_c);
+  const int j = int(jf);
+  float a = fmaf(-jf, C.c1, theta.h);  // exact
+  ff dl = two_sum(a, -jf * C.c2);      // jf * c2 exact
+  dl.l += theta.l - jf * C.c3;
+  dl = fast_two_sum(dl.h, dl.l);
+  const ff d2 = ff_sqr(dl);
+  const float d2h = d2.h;
+  // sin(delta) = delta (1 - d2/6 + d2^2/120 - d2^3/5040)
+  ff t = ff_mul(d2, C.sixth);
+  ff ps = fast_two_sum(1.0f, -t.h);
+  ps.l += -t.l + d2h * d2h * (1.0f / 120.0f - d2h * (1.0f / 5040.0f));
+  ps = norm(ps);
+  const ff sd = ff_mul(dl, ps);
+  // cos(delta) = 1 - d2/2 + d2^2/24 - d2^3/720
+  ff cd = fast_two_sum(1.0f, -0.5f * d2.h);
+  cd.l += -0.5f * d2.l + d2h * d2h * (1.0f / 24.0f - d2h * (1.0f / 720.0f));
+  cd = norm(cd);
+  const int idx = j & 127;
+  const ff S = {tab[idx][0], tab[idx][1]}, Cc = {tab[idx][2], tab[idx][3]};
+  sn = ff_add_fast(ff_mul(S, cd), ff_mul(Cc, sd));
+  cs = ff_add(ff_mul(Cc, cd), ff_neg(ff_mul(S, sd)));
+}
+
+__global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst C, double* Z, int64_t ldz) {
+  __shared__ float tab[128][4];
+  for (int e = threadIdx.x; e < 128 * 4; e += blockDim.x) tab[e >> 2][e & 3] = c_sctab[e >> 2][e & 3];
+  __syncthreads();
+  const int64_t t1 = int64_t(blockIdx.y) * 4 + (threadIdx.x >> 5);
+  const int64_t t2 = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
+  const int64_t nt = m.nt;
+  if (t1 >= nt || t2 >= nt) return;
+  int v1[3], v2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v1[a] = m.tris[3 * t1 + a];
+    v2[a] = m.tris[3 * t2 + a];
+  }
+  bool touch = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) touch |= v1[a] == v2[b];
+  if (touch) return;
+  const float* F = m.tri_ff;
+  ff yq[6][3];
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) yq[q][c] = ldff(F, nt, (q * 3 + c) * 2, t2);
+  ff D[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) D[c] = ff_add(ldff(F, nt, 36 + 2 * c, t1), ff_neg(ldff(F, nt, 36 + 2 * c, t2)));
+  CFF mu[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) mu[a][b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+  for (int p = 0; p < 6; ++p) {
+    ff E[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) E[c] = ff_add(D[c], ldff(F, nt, (p * 3 + c) * 2, t1));
+    CFF A[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) A[b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      ff dx = ff_add_fast(E[0], ff_neg(yq[q][0]));
+      ff dy = ff_add_fast(E[1], ff_neg(yq[q][1]));
+      ff dz = ff_add_fast(E[2], ff_neg(yq[q][2]));
+      ff r2 = ff_add_fast(ff_add_fast(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+      const float y0 = rsqrtf(r2.h);
+      const float s0 = r2.h * y0;
+      const float er = fmaf(-s0, s0, r2.h) + r2.l;
+      const ff r = fast_two_sum(s0, er * (0.5f * y0));
+      const ff rq = ff_mul_f(r, y0);                     // r * y0 ~ 1
+      const float corr = ((1.0f - rq.h) - rq.l) * y0;    // 1 - rq.h exact (rq.h ~ 1)
+      const ff rinv = fast_two_sum(y0, corr);
+      ff cs, sn;
+      expi_ff(ff_mul(C.k, r), C, tab, cs, sn);
+      const CFF G = {ff_mul(cs, rinv), ff_mul(sn, rinv)};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const ff wb = {c_wb[q][b][0], c_wb[q][b][1]};
+        acc_mul(A[b].r, G.r, wb);
+        acc_mul(A[b].i, G.i, wb);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      A[b].r = norm(A[b].r);
+      A[b].i = norm(A[b].i);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const ff wa = {c_wb[p][a][0], c_wb[p][a][1]};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        acc_mul(mu[a][b].r, A[b].r, wa);
+        acc_mul(mu[a][b].i, A[b].i, wa);
+      }
+    }
+  }
+  // epilogue: edge vectors e_a = P_{a+1} - P_a (a mod 3), relative to vertex 0
+  ff P1[3], P2[3], Q1[3], Q2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    P1[c] = ldff(F, nt, 42 + 2 * c, t1);
+    P2[c] = ldff(F, nt, 48 + 2 * c, t1);
+    Q1[c] = ldff(F, nt, 42 + 2 * c, t2);
+    Q2[c] = ldff(F, nt, 48 + 2 * c, t2);
+  }
+  ff eP[3][3], eQ[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    eP[0][c] = P1[c];
+    eP[1][c] = ff_add(P2[c], ff_neg(P1[c]));
+    eP[2][c] = ff_neg(P2[c]);
+    eQ[0][c] = Q1[c];
+    eQ[1][c] = ff_add(Q2[c], ff_neg(Q1[c]));
+    eQ[2][c] = ff_neg(Q2[c]);
+  }
+  ff DP[3][3];
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int be = 0; be < 3; ++be) {
+      ff s = ff_mul(eP[al][0], eQ[be][0]);
+      s = ff_add(s, ff_mul(eP[al][1], eQ[be][1]));
+      DP[al][be] = ff_add(s, ff_mul(eP[al][2], eQ[be][2]));
+    }
+  CFF I0 = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      mu[a][b].r = norm(mu[a][b].r);
+      mu[a][b].i = norm(mu[a][b].i);
+      I0.r = ff_add(I0.r, mu[a][b].r);
+      I0.i = ff_add(I0.i, mu[a][b].i);
+    }
+  ff sl1[3], sl2[3];
+  int e1[3], e2[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sl1[i] = ldff(F, nt, 54 + 2 * i, t1);
+    sl2[i] = ldff(F, nt, 54 + 2 * i, t2);
+    e1[i] = m.tri_edge[3 * t1 + i];
+    e2[i] = m.tri_edge[3 * t2 + i];
+  }
+  // (P_a - P_i) = +e_i for a = i+1, -e_{i+2} for a = i+2 (indices mod 3)
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int a1 = (i + 1) % 3, a2 = (i + 2) % 3;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int b1 = (j + 1) % 3, b2 = (j + 2) % 3;
+      CFF V = {{0.f, 0.f}, {0.f, 0.f}};
+      acc_mul(V.r, mu[a1][b1].r, DP[i][j]);
+      acc_mul(V.i, mu[a1][b1].i, DP[i][j]);
+      acc_mul(V.r, mu[a1][b2].r, ff_neg(DP[i][b2]));
+      acc_mul(V.i, mu[a1][b2].i, ff_neg(DP[i][b2]));
+      acc_mul(V.r, mu[a2][b1].r, ff_neg(DP[a2][j]));
+      acc_mul(V.i, mu[a2][b1].i, ff_neg(DP[a2][j]));
+      acc_mul(V.r, mu[a2][b2].r, DP[a2][b2]);
+      acc_mul(V.i, mu[a2][b2].i, DP[a2][b2]);
+      V.r = norm(V.r);
+      V.i = norm(V.i);
+      // -(ik/4) V + (i/k) I0 = [(k/4) V.i - (1/k) I0.i] + i [-(k/4) V.r + (1/k) I0.r]
+      const ff zr = ff_add(ff_mul(C.k4, V.i), ff_neg(ff_mul(C.kinv, I0.i)));
+      const ff zi = ff_add(ff_mul(C.kinv, I0.r), ff_neg(ff_mul(C.k4, V.r)));
+      const ff sig = ff_mul(ff_mul(sl1[i], sl2[j]), C.inv4pi);
+      double* dst = Z + 2 * (int64_t(e1[i]) * ldz + e2[j]);
+      atomicAdd(dst, to_d(ff_mul(sig, zr)));
+      atomicAdd(dst + 1, to_d(ff_mul(sig, zi)));
+    }
+  }
+}
+
+inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
+
+void split(double x, float& h, float& l) {
+  h = float(x);
+  l = float(x - double(h));
+}
+ff split_ff(double x) {
+  ff r;
+  split(x, r.h, r.l);
+  return r;
+}
+// round a double to a float with at most `bits` significant bits
+float truncate_bits(double x, int bits) {
+  int e;
+  double m = std::frexp(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
+  double scale = std::ldexp(1.0, bits);
+  return float(std::ldexp(std::nearbyint(m * scale) / scale, e));
+}
+
+}  // namespace
+
+void upload_rules_ff(const Rules& r) {
+  float tab[128][4];
+  for (int j = 0; j < 128; ++j) {
+    double th = j * M_PI / 64.0;
+    split(std::sin(th), tab[j][0], tab[j][1]);
+    split(std::cos(th), tab[j][2], tab[j][3]);
+  }
+  cudaMemcpyToSymbol(c_sctab, tab, sizeof(tab));
+  float wb[6][3][2];
+  for (int q = 0; q < 6; ++q)
+    for (int b = 0; b < 3; ++b) split(r.w[q] * r.bary[q][b], wb[q][b][0], wb[q][b][1]);
+  cudaMemcpyToSymbol(c_wb, wb, sizeof(wb));
+}
+
+// k * diameter must stay below kFFMaxPhase: the phase index j = rint(k r 64/pi) then
+// stays below 1024, which keeps j * c1 and j * c2 exact in FP32.
+double ff_max_phase() { return 48.0; }
+
+cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_t ldz, cudaStream_t s) {
+  if (k * m.diameter >= ff_max_phase()) return cudaErrorInvalidValue;
+  FFConst C;
+  C.k = split_ff(k);
+  C.k4 = split_ff(k / 4.0);
+  C.kinv = split_ff(1.0 / k);
+  C.inv4pi = split_ff(1.0 / (4.0 * M_PI));
+  C.sixth = split_ff(1.0 / 6.0);
+  const double pi64 = M_PI / 64.0;
+  C.c1 = truncate_bits(pi64, 14);
+  C.c2 = truncate_bits(pi64 - double(C.c1), 14);
+  C.c3 = float(pi64 - double(C.c1) - double(C.c2));
+  C.inv_c = float(64.0 / M_PI);
+  dim3 grid(cdiv(m.nt, 32), cdiv(m.nt, 4));
+  if (grid.y > 65535u) return cudaErrorInvalidValue;
+  efie_regular_ff_kernel<<<grid, 128, 0, s>>>(m, C, Z, ldz);
+  return launched();
+}
+
 }  // namespace fosb

@@ -57,7 +57,13 @@ struct DevMesh {
   double* tri_qp = nullptr;     // nt x 18: the 6 quadrature points (x, y, z)
   TouchPair* touch = nullptr;   // ntouch
   int32_t* ell_cols = nullptr;  // ne x 4: vertices a, b of edge m, opposite vertex in T+, in T-
+  // Float-float copies (hi, lo) for the FP32-pipe assembly, field-major: tri_ff[f * nt + t].
+  // Fields: 0..35 quadrature points minus vertex 0 ((q*3 + c)*2 + {hi,lo}); 36..41 vertex 0;
+  // 42..47 vertex 1 - vertex 0; 48..53 vertex 2 - vertex 0; 54..59 s_i l_i.
+  float* tri_ff = nullptr;
+  double diameter = 0.0;        // bounding-box diagonal
 };
+constexpr int kTriFF = 60;
 
 }  // namespace fosb
 
@@ -105,6 +111,8 @@ cudaError_t launch_rhs(const DevMesh& m, double k, const double* d_inc, int64_t 
                        int64_t ldb, cudaStream_t s);
 void upload_rules(const Rules& r);
 void upload_rules_adjoint(const Rules& r);
+void upload_rules_ff(const Rules& r);
+double ff_max_phase();  // k * mesh diameter must stay below this for the float-float kernel
 // Adjoint shape gradients (see adjoint.cu): grad (V x 3) += -grad Re sum_i lam_i^T Z u_i, and
 // += grad Re J_P for plane-wave moments with per-column parameters d_pw (ncols x 11:
 // d(3), Re pi(3), Im pi(3), alpha (re, im)) and edge weights wgt (N x ncols, ldw).

@@ -148,16 +148,21 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                : "d"(a), "d"(b));
 }
 
+// Split-K: blockIdx.z covers k in [z k_chunk, (z + 1) k_chunk); with ATOMIC the partial
+// products are added into C with FP64 atomics (C must already hold beta C).  The next
+// k-tile is fetched into registers while the current one is multiplied.
+template <bool ATOMIC>
 __global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, double ar,
                                                          double ai, const double2* __restrict__ A, int64_t lda,
                                                          const double2* __restrict__ B, int64_t ldb, double beta,
-                                                         double2* __restrict__ C, int64_t ldc) {
+                                                         double2* __restrict__ C, int64_t ldc, int64_t k_chunk) {
   __shared__ double2 As[DBM][DBK + DPA];
   __shared__ double2 Bs[DBK][DBN + DPB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3;  // warp tile origin (wm * 32, wn * 16)
   const int g = lane >> 2, t = lane & 3;
   const int64_t row0 = int64_t(blockIdx.y) * DBM, col0 = int64_t(blockIdx.x) * DBN;
+  const int64_t k_begin = int64_t(blockIdx.z) * k_chunk, k_end = min(K, k_begin + k_chunk);
   double cr[4][2][2], ci[4][2][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -165,36 +170,42 @@ __global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 2; ++e) cr[i][j][e] = ci[i][j][e] = 0.0;
-  for (int64_t k0 = 0; k0 < K; k0 += DBK) {
+  double2 ra[4], rb[4];
+  auto fetch = [&](int64_t k0) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) {  // A tile 64 x 16
       int e = tid + 256 * l;
-      int r, kk;
-      if (opA == OP_N) {
-        r = e / DBK;
-        kk = e % DBK;
-      } else {
-        kk = e / DBM;
-        r = e % DBM;
-      }
+      int r = (opA == OP_N) ? e / DBK : e % DBM;
+      int kk = (opA == OP_N) ? e % DBK : e / DBM;
       int64_t gr = row0 + r, gk = k0 + kk;
-      As[r][kk] = (gr < M && gk < K) ? load_op<double>(A, gr, gk, lda, opA) : make_double2(0.0, 0.0);
+      ra[l] = (gr < M && gk < k_end) ? load_op<double>(A, gr, gk, lda, opA) : make_double2(0.0, 0.0);
     }
 #pragma unroll
     for (int l = 0; l < 4; ++l) {  // B tile 16 x 64
       int e = tid + 256 * l;
-      int c, kk;
-      if (opB == OP_N) {
-        kk = e / DBN;
-        c = e % DBN;
-      } else {
-        c = e / DBK;
-        kk = e % DBK;
-      }
+      int c = (opB == OP_N) ? e % DBN : e / DBK;
+      int kk = (opB == OP_N) ? e / DBN : e % DBK;
       int64_t gc = col0 + c, gk = k0 + kk;
-      Bs[kk][c] = (gc < N && gk < K) ? load_op<double>(B, gk, gc, ldb, opB) : make_double2(0.0, 0.0);
+      rb[l] = (gc < N && gk < k_end) ? load_op<double>(B, gk, gc, ldb, opB) : make_double2(0.0, 0.0);
     }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      int e = tid + 256 * l;
+      int r = (opA == OP_N) ? e / DBK : e % DBM;
+      int kk = (opA == OP_N) ? e % DBK : e / DBM;
+      As[r][kk] = ra[l];
+      int c = (opB == OP_N) ? e % DBN : e / DBK;
+      int kb = (opB == OP_N) ? e / DBN : e % DBK;
+      Bs[kb][c] = rb[l];
+    }
+  };
+  if (k_begin < k_end) fetch(k_begin);
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += DBK) {
+    stage();
     __syncthreads();
+    if (k0 + DBK < k_end) fetch(k0 + DBK);  // in flight during the MMAs below
 #pragma unroll
     for (int ks = 0; ks < DBK; ks += 4) {
       double2 a[4], b[2];
@@ -226,12 +237,17 @@ __global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64
         if (c >= N) continue;
         double xr = cr[i][j][e], xi = ci[i][j][e];
         double2 v = make_double2(ar * xr - ai * xi, ar * xi + ai * xr);
-        if (beta != 0.0) {
-          double2 o = C[r * ldc + c];
-          v.x += beta * o.x;
-          v.y += beta * o.y;
+        if constexpr (ATOMIC) {
+          atomicAdd(&C[r * ldc + c].x, v.x);
+          atomicAdd(&C[r * ldc + c].y, v.y);
+        } else {
+          if (beta != 0.0) {
+            double2 o = C[r * ldc + c];
+            v.x += beta * o.x;
+            v.y += beta * o.y;
+          }
+          C[r * ldc + c] = v;
         }
-        C[r * ldc + c] = v;
       }
   }
 }
@@ -704,8 +720,26 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
   }
   if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 8) {
-    dim3 gridd(cdiv(N, DBN), cdiv(M, DBM));
-    zgemm_dmma_kernel<<<gridd, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c, ldc);
+    // split K when the output tiles alone cannot fill the GPU (tall-K, skinny products such
+    // as refinement residuals); partial products meet in C through FP64 atomics
+    const int64_t tiles = int64_t(cdiv(N, DBN)) * cdiv(M, DBM);
+    int64_t splits = 1;
+    if ((beta == 0.0 || beta == 1.0) && tiles < 2 * 152 && K >= 1024)
+      splits = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, K / 512);
+    int64_t k_chunk = ((K + splits - 1) / splits + DBK - 1) / DBK * DBK;
+    splits = (K + k_chunk - 1) / k_chunk;
+    dim3 gridd(cdiv(N, DBN), cdiv(M, DBM), unsigned(splits));
+    if (splits > 1) {
+      if (beta == 0.0) {
+        cudaError_t e = cudaMemset2DAsync(c, ldc * sizeof(V), 0, N * sizeof(V), M, s);
+        if (e != cudaSuccess) return e;
+      }
+      zgemm_dmma_kernel<true><<<gridd, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c,
+                                                    ldc, k_chunk);
+    } else {
+      zgemm_dmma_kernel<false><<<gridd, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c,
+                                                     ldc, k_chunk);
+    }
     return launched();
   }
   dim3 grid(cdiv(N, TBN), cdiv(M, TBM));

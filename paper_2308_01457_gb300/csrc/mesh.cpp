@@ -100,7 +100,7 @@ fosb_status upload(T** dst, const void* src, size_t count) {
 
 void free_dev(DevMesh& d) {
   void* ptrs[] = {d.verts,    d.vnormals,   d.tris,   d.tri_edge, d.tri_coef, d.tri_div,
-                  d.tri_area, d.tri_normal, d.tri_qp, d.touch,    d.ell_cols};
+                  d.tri_area, d.tri_normal, d.tri_qp, d.touch,    d.ell_cols, d.tri_ff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DevMesh{};
@@ -300,7 +300,33 @@ fosb_status fosb_mesh_create(const double* verts, int64_t nv, const int32_t* tri
         if (m->tri_edge[3 * t + a] == e) ell[4 * e + 2 + s] = tris[3 * t + a];
     }
   }
+  // float-float per-triangle fields (hi = nearest float, lo = nearest float of the rest)
+  std::vector<float> tff(size_t(kTriFF) * nt);
+  auto put = [&](int f, int64_t t, double x) {
+    float h = float(x);
+    tff[size_t(f) * nt + t] = h;
+    tff[size_t(f + 1) * nt + t] = float(x - double(h));
+  };
+  double lo3[3] = {1e300, 1e300, 1e300}, hi3[3] = {-1e300, -1e300, -1e300};
+  for (int64_t p = 0; p < nv; ++p)
+    for (int c = 0; c < 3; ++c) {
+      lo3[c] = std::min(lo3[c], verts[3 * p + c]);
+      hi3[c] = std::max(hi3[c], verts[3 * p + c]);
+    }
+  for (int64_t t = 0; t < nt; ++t) {
+    const int32_t* T = tris + 3 * t;
+    for (int q = 0; q < 6; ++q)
+      for (int c = 0; c < 3; ++c) put((q * 3 + c) * 2, t, qp[18 * t + 3 * q + c] - V(T[0], c));
+    for (int c = 0; c < 3; ++c) {
+      put(36 + 2 * c, t, V(T[0], c));
+      put(42 + 2 * c, t, V(T[1], c) - V(T[0], c));
+      put(48 + 2 * c, t, V(T[2], c) - V(T[0], c));
+    }
+    for (int i = 0; i < 3; ++i) put(54 + 2 * i, t, m->tri_sign[3 * t + i] * len[m->tri_edge[3 * t + i]]);
+  }
   DevMesh& d = m->d;
+  d.diameter = std::sqrt((hi3[0] - lo3[0]) * (hi3[0] - lo3[0]) + (hi3[1] - lo3[1]) * (hi3[1] - lo3[1]) +
+                         (hi3[2] - lo3[2]) * (hi3[2] - lo3[2]));
   d.nv = nv;
   d.nt = nt;
   d.ne = ne;
@@ -311,7 +337,7 @@ fosb_status fosb_mesh_create(const double* verts, int64_t nv, const int32_t* tri
       (st = upload(&d.tri_coef, coef.data(), 3 * nt)) || (st = upload(&d.tri_div, dv.data(), 3 * nt)) ||
       (st = upload(&d.tri_area, area.data(), nt)) || (st = upload(&d.tri_normal, nrm.data(), 3 * nt)) ||
       (st = upload(&d.tri_qp, qp.data(), 18 * nt)) || (st = upload(&d.touch, m->touch.data(), m->touch.size())) ||
-      (st = upload(&d.ell_cols, ell.data(), 4 * ne))) {
+      (st = upload(&d.ell_cols, ell.data(), 4 * ne)) || (st = upload(&d.tri_ff, tff.data(), tff.size()))) {
     free_dev(d);
     delete m;
     return st;

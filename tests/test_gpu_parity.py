@@ -73,6 +73,44 @@ def test_assembly_fp64_matches_oracle(name, k):
     assert np.abs(Zg - Zg.T).max() <= 1e-12 * np.abs(Zo).max()
 
 
+@pytest.mark.parametrize("name,k", [("ico1", 1.0), ("ico2", 4.0), ("torus20x8", 3.0), ("ellipsoid2", 2.5)])
+def test_assembly_float_float_matches_oracle(name, k):
+    """Float-float regular pairs (FP32 pipe) reach FP64-class accuracy: 1e-12 of max|Z|."""
+    sm = MESHES[name]()
+    m, om = _mesh(sm)
+    N = m.n_edges
+    Z = torch.zeros((N, N), dtype=C128, device=DEV)
+    F.assemble_efie(m, k, Z, arith=F.ASM_FF)
+    Zo = O.assemble_z(om, k)
+    err = np.abs(Z.cpu().numpy() - Zo).max() / np.abs(Zo).max()
+    assert err <= 1e-12, err
+
+
+def test_float_float_solution_matches_oracle():
+    sm = S.icosphere(3)
+    k = 4.0
+    m, om = _mesh(sm)
+    N = m.n_edges
+    Z = torch.zeros((N, N), dtype=C128, device=DEV)
+    b = torch.zeros((N, 1), dtype=C128, device=DEV)
+    F.assemble_efie(m, k, Z, inc=F.incidence([0, 0, 1], [1, 0, 0]), b=b, arith=F.ASM_FF)
+    lu = F.factor(Z, prec=F.MIXED)
+    u = torch.zeros_like(b)
+    F.solve(lu, b, u)
+    Zo = O.assemble_z(om, k)
+    uo = O.solve(Zo, O.rhs_planewave(om, k, [0, 0, 1], [1, 0, 0]))
+    assert _rel(u.cpu().numpy(), uo) < 1e-8
+
+
+def test_float_float_phase_range_is_checked():
+    sm = S.icosphere(1)
+    m = F.mesh_create(sm.verts, sm.tris)
+    Z = torch.zeros((m.n_edges, m.n_edges), dtype=C128, device=DEV)
+    with pytest.raises(F.FosbError) as ei:
+        F.assemble_efie(m, 30.0, Z, arith=F.ASM_FF)  # k * diameter = 60 > 48
+    assert ei.value.status == F.FOSB_ERR_INVALID_ARG
+
+
 def test_assembly_fp32_matches_oracle():
     sm = S.icosphere(2)
     m, om = _mesh(sm)
