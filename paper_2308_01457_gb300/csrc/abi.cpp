@@ -107,7 +107,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   int it = 0;
   for (;;) {
     FOSB_CUDA(copy_matrix(Bsrc, n, nrhs, ldbs, r.p, nrhs, 16, s));
-    FOSB_CUDA(gemm<double>(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s));
+    FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s));
     FOSB_TRY(col_norms(r.p, n, nrhs, nrhs, nb.as<double>(), rn, s));
     FOSB_TRY(col_norms(X, n, nrhs, ldx, nb.as<double>(), xn, s));
     berr = 0.0;
@@ -306,7 +306,8 @@ fosb_status fosb_covariance(fosb_mesh m1, fosb_lu lu1, const void* u1, fosb_mesh
   if (c64)
     e = gemm<float>(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
   else
-    e = gemm<double>(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
+    e = (prec == FOSB_MIXED ? gemm_c128_ff : gemm<double>)(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p,
+                                                           r, y2.p, r, 0.0, Sigma, lds, s);
   FOSB_CUDA(e);
   return FOSB_OK;
 }
@@ -332,8 +333,9 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
   FOSB_CUDA(launch_farfield_matrix(m1->d, k, ddirs.as<double>(), n_dir, c64, a1.p, s));
   auto G = [&](int opA, int opB, int64_t M, int64_t N, int64_t K, double ar, const void* A, int64_t lda,
                const void* B, int64_t ldb, double beta, void* C, int64_t ldc) {
-    return c64 ? gemm<float>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s)
-               : gemm<double>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+    if (c64) return gemm<float>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+    if (prec == FOSB_MIXED) return gemm_c128_ff(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+    return gemm<double>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
   };
   if (!m2) {
     FOSB_CUDA(G(OP_N, OP_N, nd3, ncols, m1->d.ne, weight, a1.p, m1->d.ne, X, ldx, accumulate ? 1.0 : 0.0, out, ldo));
@@ -384,7 +386,7 @@ fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb
   FOSB_CUDA(cudaMemsetAsync(A.p, 0, 16 * nd3 * N, s));
   FOSB_CUDA(launch_farfield_matrix(d, k, dxh.as<double>(), n, false, A.p, s));
   FOSB_CUDA(FA.alloc(16 * nd3 * n));
-  FOSB_CUDA(gemm<double>(OP_N, OP_N, nd3, n, N, 1.0, 0.0, A.p, N, U, ldu, 0.0, FA.p, n, s));
+  FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, nd3, n, N, 1.0, 0.0, A.p, N, U, ldu, 0.0, FA.p, n, s));
   std::vector<double> fa(2 * nd3 * n);
   FOSB_CUDA(cudaMemcpyAsync(fa.data(), FA.p, 16 * nd3 * n, cudaMemcpyDeviceToHost, s));
   FOSB_CUDA(cudaStreamSynchronize(s));
@@ -440,7 +442,7 @@ fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb
   FOSB_CUDA(dC.alloc(16 * nd3 * n));
   FOSB_CUDA(cudaMemcpyAsync(dC.p, Cm.data(), 16 * nd3 * n, cudaMemcpyHostToDevice, s));
   FOSB_CUDA(lam.alloc(16 * N * n));
-  FOSB_CUDA(gemm<double>(OP_T, OP_N, N, n, nd3, 1.0, 0.0, A.p, N, dC.p, n, 0.0, lam.p, n, s));
+  FOSB_CUDA(gemm_c128_ff(OP_T, OP_N, N, n, nd3, 1.0, 0.0, A.p, N, dC.p, n, 0.0, lam.p, n, s));
   FOSB_TRY(solve_internal(lu, lam.p, n, n, lam.p, n, nullptr, nullptr, s));
   FOSB_CUDA(dpw.alloc(sizeof(double) * 11 * 2 * n));
   FOSB_CUDA(cudaMemcpyAsync(dpw.p, pw.data(), sizeof(double) * 11 * 2 * n, cudaMemcpyHostToDevice, s));

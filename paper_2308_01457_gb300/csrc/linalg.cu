@@ -148,21 +148,37 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                : "d"(a), "d"(b));
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  int sz = valid ? 16 : 0;  // src-size 0: the 16 bytes are zero-filled, nothing is read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+constexpr int DSA = DBM * (DBK + DPA), DSB = DBK * (DBN + DPB);  // elements per buffer
+constexpr size_t kDmmaSmem = 2 * size_t(DSA + DSB) * sizeof(double2);
+
 // Split-K: blockIdx.z covers k in [z k_chunk, (z + 1) k_chunk); with ATOMIC the partial
-// products are added into C with FP64 atomics (C must already hold beta C).  The next
-// k-tile is fetched into registers while the current one is multiplied.
+// products are added into C with FP64 atomics (C must already hold beta C).  Tiles are
+// copied global -> shared with cp.async into two buffers: the next k-tile is in flight
+// while the current one is multiplied.  Conjugation (op C) is applied on fragment load.
 template <bool ATOMIC>
-__global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, double ar,
-                                                         double ai, const double2* __restrict__ A, int64_t lda,
-                                                         const double2* __restrict__ B, int64_t ldb, double beta,
-                                                         double2* __restrict__ C, int64_t ldc, int64_t k_chunk) {
-  __shared__ double2 As[DBM][DBK + DPA];
-  __shared__ double2 Bs[DBK][DBN + DPB];
+__global__ void __launch_bounds__(256, 2) zgemm_dmma_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K,
+                                                            double ar, double ai, const double2* __restrict__ A,
+                                                            int64_t lda, const double2* __restrict__ B, int64_t ldb,
+                                                            double beta, double2* __restrict__ C, int64_t ldc,
+                                                            int64_t k_chunk) {
+  extern __shared__ double2 dsm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3;  // warp tile origin (wm * 32, wn * 16)
   const int g = lane >> 2, t = lane & 3;
   const int64_t row0 = int64_t(blockIdx.y) * DBM, col0 = int64_t(blockIdx.x) * DBN;
   const int64_t k_begin = int64_t(blockIdx.z) * k_chunk, k_end = min(K, k_begin + k_chunk);
+  const double sa = opA == OP_C ? -1.0 : 1.0, sb = opB == OP_C ? -1.0 : 1.0;
   double cr[4][2][2], ci[4][2][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -170,15 +186,18 @@ __global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 2; ++e) cr[i][j][e] = ci[i][j][e] = 0.0;
-  double2 ra[4], rb[4];
-  auto fetch = [&](int64_t k0) {
+  auto issue = [&](int64_t k0, int buf) {
+    double2* As = dsm + buf * (DSA + DSB);
+    double2* Bs = As + DSA;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {  // A tile 64 x 16
       int e = tid + 256 * l;
       int r = (opA == OP_N) ? e / DBK : e % DBM;
       int kk = (opA == OP_N) ? e % DBK : e / DBM;
       int64_t gr = row0 + r, gk = k0 + kk;
-      ra[l] = (gr < M && gk < k_end) ? load_op<double>(A, gr, gk, lda, opA) : make_double2(0.0, 0.0);
+      bool ok = gr < M && gk < k_end;
+      const double2* src = ok ? (opA == OP_N ? A + gr * lda + gk : A + gk * lda + gr) : A;
+      cp_async16(As + r * (DBK + DPA) + kk, src, ok);
     }
 #pragma unroll
     for (int l = 0; l < 4; ++l) {  // B tile 16 x 64
@@ -186,33 +205,40 @@ __global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64
       int c = (opB == OP_N) ? e % DBN : e / DBK;
       int kk = (opB == OP_N) ? e / DBN : e % DBK;
       int64_t gc = col0 + c, gk = k0 + kk;
-      rb[l] = (gc < N && gk < k_end) ? load_op<double>(B, gk, gc, ldb, opB) : make_double2(0.0, 0.0);
+      bool ok = gc < N && gk < k_end;
+      const double2* src = ok ? (opB == OP_N ? B + gk * ldb + gc : B + gc * ldb + gk) : B;
+      cp_async16(Bs + kk * (DBN + DPB) + c, src, ok);
     }
   };
-  auto stage = [&]() {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      int e = tid + 256 * l;
-      int r = (opA == OP_N) ? e / DBK : e % DBM;
-      int kk = (opA == OP_N) ? e % DBK : e / DBM;
-      As[r][kk] = ra[l];
-      int c = (opB == OP_N) ? e % DBN : e / DBK;
-      int kb = (opB == OP_N) ? e / DBN : e % DBK;
-      Bs[kb][c] = rb[l];
+  const int64_t ntile = k_end > k_begin ? (k_end - k_begin + DBK - 1) / DBK : 0;
+  if (ntile > 0) {
+    issue(k_begin, 0);
+    cp_async_commit();
+  }
+  for (int64_t it = 0; it < ntile; ++it) {
+    if (it + 1 < ntile) {
+      issue(k_begin + (it + 1) * DBK, int((it + 1) & 1));
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
-  };
-  if (k_begin < k_end) fetch(k_begin);
-  for (int64_t k0 = k_begin; k0 < k_end; k0 += DBK) {
-    stage();
     __syncthreads();
-    if (k0 + DBK < k_end) fetch(k0 + DBK);  // in flight during the MMAs below
+    const double2* As = dsm + int(it & 1) * (DSA + DSB);
+    const double2* Bs = As + DSA;
 #pragma unroll
     for (int ks = 0; ks < DBK; ks += 4) {
       double2 a[4], b[2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[wm * 32 + i * 8 + g][ks + t];
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[(wm * 32 + i * 8 + g) * (DBK + DPA) + ks + t];
+        a[i].y *= sa;
+      }
 #pragma unroll
-      for (int j = 0; j < 2; ++j) b[j] = Bs[ks + t][wn * 16 + j * 8 + g];
+      for (int j = 0; j < 2; ++j) {
+        b[j] = Bs[(ks + t) * (DBN + DPB) + wn * 16 + j * 8 + g];
+        b[j].y *= sb;
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -249,6 +275,121 @@ __global__ void __launch_bounds__(256) zgemm_dmma_kernel(int opA, int opB, int64
           C[r * ldc + c] = v;
         }
       }
+  }
+}
+
+// ------------------------------------------------------------------ float-float complex GEMM
+// FP64-class products on the FP32 pipe: complex128 operands are split on load into
+// (hi, lo) float pairs, every real product is formed exactly with an FMA two-product,
+// accumulated with a two-sum, and the (hi, lo) accumulators are renormalised after each
+// k-tile so the low word never grows.  About 48 FP32 instructions per complex MAC
+// against ~1 TFLOP/s of FP64 throughput on this part.  Split-K with FP64 atomics as in
+// the DMMA kernel.
+__device__ __forceinline__ float4 split_c128(double2 v, double sy) {
+  float rh = float(v.x), ih = float(sy * v.y);
+  return make_float4(rh, float(v.x - double(rh)), ih, float(sy * v.y - double(ih)));
+}
+__device__ __forceinline__ void ff_acc(float& h, float& l, float xh, float xl, float yh, float yl) {
+  float p = xh * yh;
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, fmaf(xl, yh, e));
+  float s = h + p;
+  float bb = s - h;
+  l += ((h - (s - bb)) + (p - bb)) + e;
+  h = s;
+}
+
+template <bool ATOMIC>
+__global__ void __launch_bounds__(256) zgemm_ff_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, double ar,
+                                                       double ai, const double2* __restrict__ A, int64_t lda,
+                                                       const double2* __restrict__ B, int64_t ldb, double beta,
+                                                       double2* __restrict__ C, int64_t ldc, int64_t k_chunk) {
+  __shared__ float4 As[TBK * 2][TBM + 1];
+  __shared__ float4 Bs[TBK * 2][TBN + 1];
+  constexpr int KT = TBK * 2;  // 16
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t row0 = int64_t(blockIdx.y) * TBM, col0 = int64_t(blockIdx.x) * TBN;
+  const int64_t k_begin = int64_t(blockIdx.z) * k_chunk, k_end = min(K, k_begin + k_chunk);
+  const double sa = opA == OP_C ? -1.0 : 1.0, sb = opB == OP_C ? -1.0 : 1.0;
+  float4 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t k0 = k_begin; k0 < k_end; k0 += KT) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {  // A tile 64 x 16
+      int e = tid + 256 * l;
+      int r = (opA == OP_N) ? e / KT : e % TBM;
+      int kk = (opA == OP_N) ? e % KT : e / TBM;
+      int64_t gr = row0 + r, gk = k0 + kk;
+      double2 v = (gr < M && gk < k_end) ? (opA == OP_N ? A[gr * lda + gk] : A[gk * lda + gr]) : make_double2(0.0, 0.0);
+      As[kk][r] = split_c128(v, sa);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {  // B tile 16 x 64
+      int e = tid + 256 * l;
+      int c = (opB == OP_N) ? e % TBN : e / KT;
+      int kk = (opB == OP_N) ? e / TBN : e % KT;
+      int64_t gc = col0 + c, gk = k0 + kk;
+      double2 v = (gc < N && gk < k_end) ? (opB == OP_N ? B[gk * ldb + gc] : B[gc * ldb + gk]) : make_double2(0.0, 0.0);
+      Bs[kk][c] = split_c128(v, sb);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KT; ++kk) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float4& c = acc[i][j];  // (re.h, re.l, im.h, im.l)
+          ff_acc(c.x, c.y, a[i].x, a[i].y, b[j].x, b[j].y);
+          ff_acc(c.x, c.y, -a[i].z, -a[i].w, b[j].z, b[j].w);
+          ff_acc(c.z, c.w, a[i].x, a[i].y, b[j].z, b[j].w);
+          ff_acc(c.z, c.w, a[i].z, a[i].w, b[j].x, b[j].y);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // renormalise (fast two-sum)
+        float4& c = acc[i][j];
+        float s = c.x + c.y;
+        c.y = c.y - (s - c.x);
+        c.x = s;
+        s = c.z + c.w;
+        c.w = c.w - (s - c.z);
+        c.z = s;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t r = row0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t c = col0 + tx + 16 * j;
+      if (c >= N) continue;
+      double xr = double(acc[i][j].x) + double(acc[i][j].y), xi = double(acc[i][j].z) + double(acc[i][j].w);
+      double2 v = make_double2(ar * xr - ai * xi, ar * xi + ai * xr);
+      if constexpr (ATOMIC) {
+        atomicAdd(&C[r * ldc + c].x, v.x);
+        atomicAdd(&C[r * ldc + c].y, v.y);
+      } else {
+        if (beta != 0.0) {
+          double2 o = C[r * ldc + c];
+          v.x += beta * o.x;
+          v.y += beta * o.y;
+        }
+        C[r * ldc + c] = v;
+      }
+    }
   }
 }
 
@@ -729,16 +870,24 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
     int64_t k_chunk = ((K + splits - 1) / splits + DBK - 1) / DBK * DBK;
     splits = (K + k_chunk - 1) / k_chunk;
     dim3 gridd(cdiv(N, DBN), cdiv(M, DBM), unsigned(splits));
+    static bool smem_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+      cudaFuncSetAttribute(zgemm_dmma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kDmmaSmem));
+      cudaFuncSetAttribute(zgemm_dmma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kDmmaSmem));
+      smem_set[dev] = true;
+    }
     if (splits > 1) {
       if (beta == 0.0) {
         cudaError_t e = cudaMemset2DAsync(c, ldc * sizeof(V), 0, N * sizeof(V), M, s);
         if (e != cudaSuccess) return e;
       }
-      zgemm_dmma_kernel<true><<<gridd, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c,
-                                                    ldc, k_chunk);
+      zgemm_dmma_kernel<true><<<gridd, 256, kDmmaSmem, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb,
+                                                            beta, c, ldc, k_chunk);
     } else {
-      zgemm_dmma_kernel<false><<<gridd, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c,
-                                                     ldc, k_chunk);
+      zgemm_dmma_kernel<false><<<gridd, 256, kDmmaSmem, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb,
+                                                             beta, c, ldc, k_chunk);
     }
     return launched();
   }
@@ -749,6 +898,40 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
 
 template cudaError_t gemm<double>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
                                   const void*, int64_t, double, void*, int64_t, cudaStream_t);
+
+cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im,
+                         const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                         cudaStream_t s) {
+  using V = double2;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  // up to 8 right-hand sides: the FP64 row-per-warp kernel streams A once and is faster
+  // than a 64-wide tile that would be mostly padding
+  if (K <= 0 || (opA == OP_N && N <= 8))
+    return gemm<double>(opA, opB, M, N, K, alpha_re, alpha_im, A, lda, B, ldb, beta, C, ldc, s);
+  if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
+  const V* a = static_cast<const V*>(A);
+  const V* b = static_cast<const V*>(B);
+  V* c = static_cast<V*>(C);
+  const int64_t tiles = int64_t(cdiv(N, TBN)) * cdiv(M, TBM);
+  int64_t splits = 1;
+  if ((beta == 0.0 || beta == 1.0) && tiles < 4 * 152 && K >= 1024)
+    splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 512);
+  int64_t k_chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+  splits = (K + k_chunk - 1) / k_chunk;
+  dim3 grid(cdiv(N, TBN), cdiv(M, TBM), unsigned(splits));
+  if (splits > 1) {
+    if (beta == 0.0) {
+      cudaError_t e = cudaMemset2DAsync(c, ldc * sizeof(V), 0, N * sizeof(V), M, s);
+      if (e != cudaSuccess) return e;
+    }
+    zgemm_ff_kernel<true><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c, ldc,
+                                               k_chunk);
+  } else {
+    zgemm_ff_kernel<false><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c, ldc,
+                                                k_chunk);
+  }
+  return launched();
+}
 template cudaError_t gemm<float>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
                                  const void*, int64_t, double, void*, int64_t, cudaStream_t);
 
