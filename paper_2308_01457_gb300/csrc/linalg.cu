@@ -984,7 +984,11 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
       enable_trsv_smem<T>();
       trsv_warp_kernel<T><<<cdiv(rest, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
       note_launches(1);
-      e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0, Ap + jb * lda + jb, lda, s);
+      if constexpr (sizeof(T) == 4)  // complex64 factors: tensor cores (tcgen05, 3xTF32)
+        e = cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s);
+      else
+        e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0, Ap + jb * lda + jb,
+                    lda, s);
       if (e != cudaSuccess) {
         st = cuda_fail(e, "getrf: trailing update");
         break;
@@ -1044,7 +1048,10 @@ fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ip
       enable_trsv_smem<T>();
       trsv_warp_kernel<T><<<cdiv(rest, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
       note_launches(1);
-      FOSB_CUDA(gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0,
+      if constexpr (sizeof(T) == 4)
+        FOSB_CUDA(cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s));
+      else
+        FOSB_CUDA(gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0,
                         Ap + jb * lda + jb, lda, s));
     }
     FOSB_CUDA(cudaGetLastError());
