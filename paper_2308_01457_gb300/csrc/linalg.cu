@@ -624,6 +624,142 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::ty
   }
 }
 
+// The same panel factorisation with each CTA's row block resident in shared memory
+// (rows [lo, hi) x jb, loaded once, written back once); only the pivot candidates, the
+// pivot row and row j cross CTAs, through global memory and the bounded grid barrier.
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(typename C2<T>::type* A, int64_t m, int jb,
+                                                                   int64_t lda, int32_t* ipiv, int64_t row_base,
+                                                                   PanelScratch* scr, double* cand_val,
+                                                                   int64_t* cand_row, typename C2<T>::type* cand_data,
+                                                                   typename C2<T>::type* rowj, int* status) {
+  using V = typename C2<T>::type;
+  extern __shared__ unsigned char panel_raw[];
+  V* sP = reinterpret_cast<V*>(panel_raw);  // (hi - lo) x jb
+  const unsigned G = gridDim.x;
+  const int64_t chunk = (m + G - 1) / G;
+  const int64_t lo = int64_t(blockIdx.x) * chunk, hi = min(m, lo + chunk);
+  const int nr = hi > lo ? int(hi - lo) : 0;
+  __shared__ double s_val[kPanelThreads / 32];
+  __shared__ int64_t s_row[kPanelThreads / 32];
+  __shared__ V s_piv[64];
+  __shared__ int64_t s_p;
+  __shared__ int s_win;
+  for (int e = threadIdx.x; e < nr * jb; e += blockDim.x) sP[e] = A[(lo + e / jb) * lda + e % jb];
+  __syncthreads();
+  for (int j = 0; j < jb; ++j) {
+    const int par = j & 1;
+    double best = -1.0;
+    int64_t brow = m;
+    for (int r = (j > lo ? int(j - lo) : 0) + threadIdx.x; r < nr; r += blockDim.x) {
+      V v = sP[r * jb + j];
+      double a = fabs(double(v.x)) + fabs(double(v.y));
+      if (a > best) {
+        best = a;
+        brow = lo + r;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, off);
+      int64_t orow = __shfl_xor_sync(0xffffffffu, brow, off);
+      if (ob > best || (ob == best && orow < brow)) {
+        best = ob;
+        brow = orow;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_val[threadIdx.x >> 5] = best;
+      s_row[threadIdx.x >> 5] = brow;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kPanelThreads / 32; ++w)
+        if (s_val[w] > best || (s_val[w] == best && s_row[w] < brow)) {
+          best = s_val[w];
+          brow = s_row[w];
+        }
+      s_val[0] = best;
+      s_row[0] = brow;
+      cand_val[par * G + blockIdx.x] = best;
+      cand_row[par * G + blockIdx.x] = brow;
+    }
+    __syncthreads();
+    brow = s_row[0];
+    for (int c = threadIdx.x; c < jb; c += blockDim.x) {
+      cand_data[(int64_t(par) * G + blockIdx.x) * jb + c] = (brow < m) ? sP[(brow - lo) * jb + c] : V{T(0), T(0)};
+      if (j >= lo && j < hi) rowj[par * jb + c] = sP[(j - lo) * jb + c];
+    }
+    __threadfence();
+    if (!grid_barrier(&scr->count, &scr->gen, G, status)) return;
+    if (threadIdx.x < 32) {
+      double b = -1.0;
+      int64_t r = m;
+      int win = 0;
+      for (unsigned g = threadIdx.x; g < G; g += 32) {
+        double v = ((volatile double*)cand_val)[par * G + g];
+        int64_t rr = ((volatile int64_t*)cand_row)[par * G + g];
+        if (v > b || (v == b && rr < r)) {
+          b = v;
+          r = rr;
+          win = int(g);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, b, off);
+        int64_t orow = __shfl_xor_sync(0xffffffffu, r, off);
+        int ow = __shfl_xor_sync(0xffffffffu, win, off);
+        if (ob > b || (ob == b && orow < r)) {
+          b = ob;
+          r = orow;
+          win = ow;
+        }
+      }
+      if (threadIdx.x == 0) {
+        s_p = r;
+        s_win = win;
+        if (blockIdx.x == 0) {
+          ipiv[j] = int32_t(row_base + r);
+          if (!(b > 0.0)) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    const V* pdata = cand_data + (int64_t(par) * G + s_win) * jb;
+    for (int c = threadIdx.x; c < jb; c += blockDim.x) s_piv[c] = __ldcg(pdata + c);
+    __syncthreads();
+    if (p != j) {
+      if (j >= lo && j < hi)
+        for (int c = threadIdx.x; c < jb; c += blockDim.x) sP[(j - lo) * jb + c] = s_piv[c];
+      if (p >= lo && p < hi)
+        for (int c = threadIdx.x; c < jb; c += blockDim.x) sP[(p - lo) * jb + c] = __ldcg(rowj + par * jb + c);
+    }
+    __syncthreads();
+    const V pv = s_piv[j];
+    const T den = pv.x * pv.x + pv.y * pv.y;
+    const V inv = den > T(0) ? V{pv.x / den, -pv.y / den} : V{T(0), T(0)};
+    const int r0 = (int64_t(j) + 1 > lo) ? int(int64_t(j) + 1 - lo) : 0;
+    for (int r = r0 + threadIdx.x; r < nr; r += blockDim.x) sP[r * jb + j] = cmul<T>(sP[r * jb + j], inv);
+    __syncthreads();
+    const int ncols = jb - j - 1;
+    if (ncols > 0 && nr > r0) {
+      const int total = (nr - r0) * ncols;
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = r0 + e / ncols, c = j + 1 + e % ncols;
+        V l = sP[r * jb + j], u = s_piv[c];
+        V a = sP[r * jb + c];
+        a.x -= l.x * u.x - l.y * u.y;
+        a.y -= l.x * u.y + l.y * u.x;
+        sP[r * jb + c] = a;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nr * jb; e += blockDim.x) A[(lo + e / jb) * lda + e % jb] = sP[e];
+}
+
 // Row swaps of the block row [j0, j0 + jb) applied to columns outside the panel.
 template <typename T>
 __global__ void laswp_kernel(typename C2<T>::type* A, int64_t n, int64_t lda, int64_t j0, int jb,
@@ -827,6 +963,43 @@ __global__ void copy_kernel(const T* s, int64_t rows, int64_t cols, int64_t lds,
   d[i * ldd + j] = s[i * lds + j];
 }
 
+// Launch one panel factorisation (m x jb at Ap): the shared-memory-resident kernel when
+// each CTA's row block fits in 200 KB, otherwise the global-memory kernel.
+constexpr int kPanelSmemBudget = 200 * 1024;
+
+template <typename T>
+cudaError_t launch_panel(typename C2<T>::type* Ap, int64_t m, int jb, int64_t lda, int32_t* ip, int64_t row_base,
+                         PanelScratch* scr, double* cand_val, int64_t* cand_row, typename C2<T>::type* cand_data,
+                         typename C2<T>::type* rowj, int* d_status, int64_t G_cap, int nsm, cudaStream_t s) {
+  using V = typename C2<T>::type;
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaFuncSetAttribute(panel_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemBudget);
+    attr[dev] = true;
+  }
+  const int64_t rows_cap = kPanelSmemBudget / (int64_t(jb) * int64_t(sizeof(V)));
+  int64_t G = std::min<int64_t>(std::min<int64_t>(G_cap, nsm),
+                                std::max<int64_t>((m + rows_cap - 1) / rows_cap, (m + 255) / 256));
+  G = std::max<int64_t>(G, 1);
+  const int64_t chunk = (m + G - 1) / G;
+  const size_t smem = size_t(chunk) * jb * sizeof(V);
+  int per_sm = 0;
+  if (chunk <= rows_cap &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_smem_kernel<T>, kPanelThreads, smem) == cudaSuccess &&
+      per_sm >= 1 && G <= int64_t(per_sm) * nsm) {
+    void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_smem_kernel<T>), dim3(unsigned(G)),
+                                       dim3(kPanelThreads), args, smem, s);
+  }
+  G = std::min<int64_t>(std::min<int64_t>(G_cap, nsm), std::max<int64_t>(1, (m + 255) / 256));
+  if ((m + G - 1) / G > kMaxPanelRows) return cudaErrorInvalidValue;
+  void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)), dim3(kPanelThreads),
+                                     args, 0, s);
+}
+
 }  // namespace
 
 template <typename T>
@@ -962,17 +1135,10 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
   for (int64_t j0 = 0; j0 < n && st == FOSB_OK; j0 += nb) {
     int jb = int(std::min<int64_t>(nb, n - j0));
     int64_t m = n - j0;
-    int64_t G = std::min<int64_t>(int64_t(G_cap), std::max<int64_t>(1, (m + 63) / 64));
-    if ((m + G - 1) / G > kMaxPanelRows) {
-      st = fail(FOSB_ERR_INVALID_ARG, "getrf: matrix too large for the panel kernel");
-      break;
-    }
     V* Ap = A + j0 * lda + j0;
     int32_t* ip = ipiv + j0;
-    int64_t base = j0;
-    void* args[] = {&Ap, &m, &jb, &lda, &ip, &base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
-    cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)),
-                                                dim3(kPanelThreads), args, 0, s);
+    cudaError_t e = launch_panel<T>(Ap, m, jb, lda, ip, j0, scr, cand_val, cand_row, cand_data, rowj, d_status,
+                                    int64_t(G_cap), nsm, s);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "getrf: cooperative panel launch");
       break;
@@ -1033,14 +1199,9 @@ fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ip
   for (int64_t j0 = 0; j0 < n; j0 += nb) {
     int jb = int(std::min<int64_t>(nb, n - j0));
     int64_t m = n - j0;
-    int64_t G = std::min<int64_t>(G_cap, std::max<int64_t>(1, (m + 63) / 64));
-    if ((m + G - 1) / G > kMaxPanelRows) return fail(FOSB_ERR_INVALID_ARG, "getrf: matrix too large for the panel kernel");
     V* Ap = A + j0 * lda + j0;
     int32_t* ip = ipiv + j0;
-    int64_t row_base = j0;
-    void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
-    FOSB_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)),
-                                          dim3(kPanelThreads), args, 0, s));
+    FOSB_CUDA(launch_panel<T>(Ap, m, jb, lda, ip, j0, scr, cand_val, cand_row, cand_data, rowj, d_status, G_cap, nsm, s));
     laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
     note_launches(2);
     int64_t rest = n - j0 - jb;

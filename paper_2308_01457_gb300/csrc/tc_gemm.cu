@@ -100,9 +100,10 @@ __device__ __forceinline__ void store_split(unsigned char* base, int off, float2
   *reinterpret_cast<float*>(base + 3 * PART + off) = tf32_round(v.y - ib);
 }
 
-__global__ void __launch_bounds__(256) cgemm_update_tc_kernel(int64_t M, int64_t N, int64_t K, const float2* __restrict__ A,
+__global__ void __launch_bounds__(256, 2) cgemm_update_tc_kernel(int64_t M, int64_t N, int64_t K, const float2* __restrict__ A,
                                                               int64_t lda, const float2* __restrict__ B, int64_t ldb,
-                                                              float2* __restrict__ C, int64_t ldc, int* status) {
+                                                              float2* __restrict__ C, int64_t ldc, int* status,
+                                                              int vec_ok) {
   extern __shared__ unsigned char tc_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sA = smem;           // 4 parts x 2 slabs x 4096
@@ -131,27 +132,38 @@ __global__ void __launch_bounds__(256) cgemm_update_tc_kernel(int64_t M, int64_t
   const uint32_t d_re = tmem, d_im = tmem + TC_N;
   uint32_t phase = 0;
   const int64_t nchunk = (K + TC_KC - 1) / TC_KC;
-  for (int64_t ch = 0; ch < nchunk; ++ch) {
-    const int64_t k0 = ch * TC_KC;
-    // ---- stage A (128 x 16 complex): e -> (k8, row & 7, slab, row >> 3); 8 consecutive
-    // threads read 64 contiguous bytes of one row
-#pragma unroll 4
+  // Staging maps (per 32-lane group: k3 = lane & 3, rc = lane >> 2): every warp load covers
+  // 8 rows x 4 consecutive k (A) or 4 k-rows x 8 consecutive columns (B) -- whole 32-byte
+  // sectors -- and the K-major store offsets (rc * 16 + k3 * 4 within a core matrix) hit 32
+  // distinct banks.
+  const int k3 = lane & 3, rc = lane >> 2;
+  float2 va[8], vb[8];
+  auto load_chunk = [&](int64_t k0) {
+#pragma unroll
     for (int it = 0; it < 8; ++it) {
-      const int e = tid + 256 * it;
-      const int k8 = e & 7, rlo = (e >> 3) & 7, slab = (e >> 6) & 1, rg = e >> 7;
-      const int r = rg * 8 + rlo, kk = slab * 8 + k8;
+      const int w = warp + 8 * it;                       // 0..63
+      const int khi = w & 3, rg = w >> 2;                // A: k-quad, 8-row group
+      const int r = rg * 8 + rc, kk = (khi >> 1) * 8 + (khi & 1) * 4 + k3;
       const int64_t gr = row0 + r, gk = k0 + kk;
-      const float2 v = (gr < M && gk < K) ? A[gr * lda + gk] : make_float2(0.f, 0.f);
-      store_split(sA, slab * SLAB + kmajor_off(r, k8), v);
+      va[it] = (gr < M && gk < K) ? A[gr * lda + gk] : make_float2(0.f, 0.f);
+      const int cg = w & 15, kb = w >> 4;                // B: 8-column group, k-quad
+      const int c = cg * 8 + rc, kkb = (kb >> 1) * 8 + (kb & 1) * 4 + k3;
+      const int64_t gc = col0 + c, gkb = k0 + kkb;
+      vb[it] = (gc < N && gkb < K) ? B[gkb * ldb + gc] : make_float2(0.f, 0.f);
     }
-    // ---- stage B (16 x 128 complex, row-major) as the K-major 128 x 16 operand
-#pragma unroll 4
+  };
+  if (nchunk > 0) load_chunk(0);
+  for (int64_t ch = 0; ch < nchunk; ++ch) {
+    // ---- split and store the chunk held in registers (K-major, canonical layout)
+#pragma unroll
     for (int it = 0; it < 8; ++it) {
-      const int e = tid + 256 * it;
-      const int c = e & 127, kk = e >> 7;
-      const int64_t gc = col0 + c, gk = k0 + kk;
-      const float2 v = (gc < N && gk < K) ? B[gk * ldb + gc] : make_float2(0.f, 0.f);
-      store_split(sB, (kk >> 3) * SLAB + kmajor_off(c, kk & 7), v);
+      const int w = warp + 8 * it;
+      const int khi = w & 3, rg = w >> 2;
+      const int r = rg * 8 + rc, k8 = (khi & 1) * 4 + k3;
+      store_split(sA, (khi >> 1) * SLAB + kmajor_off(r, k8), va[it]);
+      const int cg = w & 15, kb = w >> 4;
+      const int c = cg * 8 + rc, k8b = (kb & 1) * 4 + k3;
+      store_split(sB, (kb >> 1) * SLAB + kmajor_off(c, k8b), vb[it]);
     }
     asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor core
     __syncthreads();
@@ -183,6 +195,8 @@ __global__ void __launch_bounds__(256) cgemm_update_tc_kernel(int64_t M, int64_t
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr));
     }
+    // the next chunk's global loads are in flight while the MMAs run
+    if (ch + 1 < nchunk) load_chunk((ch + 1) * TC_KC);
     // all threads wait for the MMAs (shared memory is reused by the next chunk)
     if (!mbar_wait(mbar_addr, phase)) abort_sh = 1;
     phase ^= 1u;
@@ -209,18 +223,48 @@ __global__ void __launch_bounds__(256) cgemm_update_tc_kernel(int64_t M, int64_t
 #pragma unroll
       for (int j = 0; j < 32; ++j) sE[r_local * EPI_LD + csub + j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
       __syncthreads();
-      // coalesced update: a warp covers one row's 64 complex (512 B) per pass
-#pragma unroll 4
-      for (int it = 0; it < 32; ++it) {
-        const int e = tid + 256 * it;  // 0 .. 8191
-        const int r = e >> 6, c = e & 63;
-        const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
-        if (gr < M && gc < N) {
-          const float2 d = sE[r * EPI_LD + c];
-          float2 o = C[gr * ldc + gc];
-          o.x -= d.x;
-          o.y -= d.y;
-          C[gr * ldc + gc] = o;
+      // coalesced update: a warp covers one row's 64 complex (512 B) per pass; all loads
+      // are issued before any store
+      if (vec_ok) {
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+        float4 o[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int e = tid + 256 * (it + 8 * pass);  // 0 .. 4095 pairs of complex
+          const int r = e >> 5, c = (e & 31) * 2;
+          const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+          o[it] = (gr < M && gc + 1 < N) ? *reinterpret_cast<const float4*>(C + gr * ldc + gc) : make_float4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int e = tid + 256 * (it + 8 * pass);
+          const int r = e >> 5, c = (e & 31) * 2;
+          const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+          if (gr < M && gc + 1 < N) {
+            const float2 d0 = sE[r * EPI_LD + c], d1 = sE[r * EPI_LD + c + 1];
+            *reinterpret_cast<float4*>(C + gr * ldc + gc) =
+                make_float4(o[it].x - d0.x, o[it].y - d0.y, o[it].z - d1.x, o[it].w - d1.y);
+          } else if (gr < M && gc < N) {  // ragged last column
+            float2 v = C[gr * ldc + gc];
+            const float2 d0 = sE[r * EPI_LD + c];
+            C[gr * ldc + gc] = make_float2(v.x - d0.x, v.y - d0.y);
+          }
+        }
+        }
+      } else {
+#pragma unroll 8
+        for (int it = 0; it < 32; ++it) {
+          const int e = tid + 256 * it;  // 0 .. 8191
+          const int r = e >> 6, c = e & 63;
+          const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+          if (gr < M && gc < N) {
+            const float2 d = sE[r * EPI_LD + c];
+            float2 o = C[gr * ldc + gc];
+            o.x -= d.x;
+            o.y -= d.y;
+            C[gr * ldc + gc] = o;
+          }
         }
       }
       __syncthreads();
@@ -249,9 +293,11 @@ cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int6
   }
   dim3 grid(cdiv(N, TC_N), cdiv(M, TC_M));
   if (grid.y > 65535u) return cudaErrorInvalidValue;
+  // 16-byte epilogue accesses need a 16-byte aligned C with an even leading dimension
+  const int vec_ok = (reinterpret_cast<uintptr_t>(C) % 16 == 0) && (ldc % 2 == 0);
   cgemm_update_tc_kernel<<<grid, 256, TC_SMEM, s>>>(M, N, K, static_cast<const float2*>(A), lda,
                                                    static_cast<const float2*>(B), ldb, static_cast<float2*>(C), ldc,
-                                                   status);
+                                                   status, vec_ok);
   return launched();
 }
 
