@@ -32,7 +32,8 @@ METRIC = "FOSB covariance time & EFIE entries/s, mixed vs FP64 on one GB300 at 1
 WORKLOADS = {
     # mixed-precision sphere, levels l = 0..4 are icospheres of T = 80 * 4**l triangles
     "sphere-ka4-ct-L4": dict(levels=[0, 1, 2, 3, 4], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=4),
-    # small case of the same kernels (profiling captures)
+    # smaller cases of the same kernels (profiling captures)
+    "sphere-ka4-ct-L3": dict(levels=[0, 1, 2, 3], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=3),
     "sphere-ka4-ct-L2": dict(levels=[0, 1, 2], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=2),
 }
 
@@ -40,6 +41,10 @@ WORKLOADS = {
 # FP64 nominal of the part.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
+# DRAM bytes (read + write) per complex64 output element of one tcgen05 LU-update launch,
+# from the ncu capture summarised in profiles/ (C is read and written once: 16 B algorithmic)
+LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (472.180480e6 + 403.065856e6) / 7616.0**2  # 15.09 B
 
 
 def _peaks():
@@ -139,6 +144,10 @@ def run_fosb(args):
     timers = {}
     launches0 = F.lib().fosb_kernel_launches()
     clocks = _clock_sampler(local) if rank == 0 else None
+    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff"]
+    for fam in families:  # clear earlier records
+        F.lib().fosb_profile_read(fam.encode(), None, None, None)
+    F.lib().fosb_profile_enable(1)
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start.record()
     for _ in range(args.steps):
@@ -146,8 +155,17 @@ def run_fosb(args):
         prob.release()
     t_end.record()
     barrier()
+    F.lib().fosb_profile_enable(0)
     clk = _clock_summary(clocks)
     launches = int(F.lib().fosb_kernel_launches() - launches0)
+    import ctypes
+
+    fam_stats = {}
+    for fam in families:
+        ms_c, n_c, w_c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        F.lib().fosb_profile_read(fam.encode(), ctypes.byref(ms_c), ctypes.byref(n_c), ctypes.byref(w_c))
+        fam_stats[fam] = {"ms_per_step": ms_c.value / args.steps, "launches_per_step": n_c.value / args.steps,
+                          "work_per_step": w_c.value / args.steps}
     ms = t_start.elapsed_time(t_end) / args.steps
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
@@ -164,27 +182,46 @@ def run_fosb(args):
     t_cov = avg("covariance_ct")
     NL = N[L]
     T = prob.levels[L].mesh.nt
-    ntouch = prob.levels[L].mesh.n_touching
-    regular_pairs = T * T - (2 * ntouch - T)
-    asm_flops = 27.0 * 36.0 * regular_pairs  # algorithmic FP ops per point pair x point pairs
-    lu_flops = 8.0 / 3.0 * NL**3
     peaks = _peaks()
-    rows = {
-        "assemble": dict(ms=t_asm, flops=asm_flops, peak=FP32_PEAK_TFLOPS if arith == F.ASM_FF else FP64_PEAK_TFLOPS,
-                         kernel="efie_regular_ff" if arith == F.ASM_FF else "efie_regular_kernel<double>",
-                         note="FP32 peak (float-float)" if arith == F.ASM_FF else "FP64 nominal peak"),
-        "factor": dict(ms=t_fac, flops=lu_flops, peak=FP32_PEAK_TFLOPS, kernel="gemm_tiled_kernel<float> (LU)",
-                       note="FP32 SIMT derived peak"),
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tf32_peak = bf16 * TF32_PER_BF16  # measured bf16 burst x nominal TF32/bf16 ratio
+    # algorithmic work -> (bound, flops, peak, kernel, note) per family
+    fam_model = {
+        "lu_update": ("tensor", 1.0, tf32_peak, "cgemm_update_tc_kernel (tcgen05 kind::tf32, 3xTF32 complex)",
+                      f"TF32 dense = measured bf16 {bf16} x 1.1/2.25; work = useful complex flops 8MNK "
+                      "(3xTF32 executes 3x that on the tensor pipe, so frac <= 1/3)"),
+        "asm_regular": ("alu", 27.0, FP32_PEAK_TFLOPS if arith == F.ASM_FF else FP64_PEAK_TFLOPS,
+                        "efie_regular_ff_kernel" if arith == F.ASM_FF else "efie_regular_kernel<double>",
+                        "27 algorithmic FP ops per point pair; FP32 pipe peak 152 SMs x 128 lanes x 2 x 2.07 GHz"
+                        if arith == F.ASM_FF else "27 algorithmic FP ops per point pair; FP64 nominal peak"),
+        "gemm_ff": ("alu", 1.0, FP32_PEAK_TFLOPS, "zgemm_ff_kernel (float-float complex128 GEMM)",
+                    "work = complex128 flops 8MNK executed as ~48 FP32 instructions per complex MAC"),
+        "lu_panel": ("latency", 1.0, None, "panel_smem_kernel<float> (cooperative, grid barrier per column)",
+                     "latency-bound: one grid barrier per column"),
     }
-    dom = max(rows, key=lambda r: rows[r]["ms"])
-    R = rows[dom]
-    achieved = R["flops"] / (R["ms"] * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(R["peak"], 2), "unit": "TFLOP/s",
-                "frac": round(achieved / R["peak"], 4), "traffic": None, "kernel": R["kernel"],
-                "call": f"fosb_{'assemble_efie' if dom == 'assemble' else 'factor'} level {L} (N={NL})",
-                "peak_source": R["note"] + " (derived, not in MEASURED_PEAKS.json)"}
-    secondary = {k: {"ms": round(v["ms"], 2), "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3)}
-                 for k, v in rows.items()}
+    dom = max((f for f in fam_model if fam_stats[f]["ms_per_step"] > 0),
+              key=lambda f: fam_stats[f]["ms_per_step"], default="lu_update")
+    bound, wscale, peak, kname, note = fam_model[dom]
+    st = fam_stats[dom]
+    achieved = st["work_per_step"] * wscale / (st["ms_per_step"] * 1e-3) / 1e12 if st["ms_per_step"] > 0 else 0.0
+    roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2) if peak else None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None,
+                "traffic": None, "kernel": kname, "family": dom,
+                "ms_per_step": round(st["ms_per_step"], 2), "launches_per_step": st["launches_per_step"],
+                "peak_source": note + " (of measured)" if bound == "tensor" else note}
+    if dom == "lu_update" and st["launches_per_step"] > 0:
+        # DRAM bytes per launch from the ncu capture (bytes per output element of C, see
+        # profiles/), scaled to the average launch of the timed region (K = 64)
+        avg_outputs = st["work_per_step"] / (8.0 * 64.0 * st["launches_per_step"])
+        if LU_UPDATE_DRAM_BYTES_PER_OUTPUT is not None:
+            roofline["traffic"] = round(LU_UPDATE_DRAM_BYTES_PER_OUTPUT * avg_outputs)
+        roofline["algorithmic_bytes"] = round(16.0 * avg_outputs)
+    secondary = {}
+    for f, (b, wsc, pk, kn, _) in fam_model.items():
+        s_ = fam_stats[f]
+        rate = s_["work_per_step"] * wsc / (s_["ms_per_step"] * 1e-3) / 1e12 if s_["ms_per_step"] > 0 else 0.0
+        secondary[f] = {"ms_per_step": round(s_["ms_per_step"], 2), "launches_per_step": s_["launches_per_step"],
+                        "tflops": round(rate, 3), "frac": round(rate / pk, 4) if pk else None}
     # IR quality (refined path must reach FP64 backward error)
     berr = max(prob.levels[l].berr for l in prob.levels)
     e2e = run_e2e(args, W, meshes, dirs, arith) if (rank == 0 and not args.no_e2e) else None
@@ -193,7 +230,9 @@ def run_fosb(args):
     line = {
         "metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per FOSB step", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 LU + f64 refinement/assembly (mixed)", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "mixed: 3xTF32 tensor-core LU (c64 factors), float-float (f32x2) assembly and FP64-class "
+                 "refinement residuals, f64 singular quadrature", "data": "synthetic",
         "config": {"workload": args.workload, "levels": W["levels"], "N_levels": [N[l] for l in sorted(N)],
                    "triangles_finest": T, "k": W["k"], "n_dir": W["n_dir"], "ct": [W["L0"], W["L"]],
                    "assembly": args.arith, "parallelism": f"replicas{ws}",

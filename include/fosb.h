@@ -112,6 +112,19 @@ const char* fosb_version(void);
  * diagnostics for launch accounting. */
 uint64_t fosb_kernel_launches(void);
 
+/* Kernel-family timing (diagnostics).  While enabled, the library brackets every launch of
+ * the families below with CUDA events recorded on the launching stream and notes the
+ * launch's algorithmic work.  fosb_profile_read waits for the recorded events and returns
+ * (then clears) the family's total device time in ms, launch count and work:
+ *   "lu_update"      tcgen05 complex64 trailing update, work = 8 M N K flops
+ *   "lu_panel"       cooperative panel factorisation, work = 8 m jb^2 / 2 flops
+ *   "asm_regular"    regular-pair assembly, work = point pairs (36 per triangle pair)
+ *   "asm_singular"   Sauter-Schwab pairs, work = point pairs
+ *   "gemm_ff"        float-float complex128 GEMM, work = 8 M N K flops
+ * Any pointer may be NULL. */
+fosb_status fosb_profile_enable(int on);
+fosb_status fosb_profile_read(const char* family, double* total_ms, int64_t* launches, double* work);
+
 /* ---- A1: mesh tables ------------------------------------------------------------
  * Builds the RWG tables of a closed, orientable, manifold triangulation (Section IV,
  * meshes Gamma_{h_l} of planar triangles) and uploads them to the current device.

@@ -67,7 +67,7 @@ def lib():
         for name in ("fosb_mesh_create", "fosb_mesh_info", "fosb_mesh_edges", "fosb_mesh_destroy",
                      "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
                      "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
-                     "fosb_getrf_static"):
+                     "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib

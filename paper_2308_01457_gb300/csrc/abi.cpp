@@ -77,7 +77,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   }
   if (lu->prec == FOSB_FP32) {
     if (X != B) FOSB_CUDA(copy_matrix(B, n, nrhs, ldb, X, ldx, 8, s));
-    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, X, nrhs, ldx, s));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, X, nrhs, ldx, s, lu->d_status));
     return FOSB_OK;
   }
   // MIXED: complex64 factors, FP64 residuals.
@@ -101,7 +101,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   FOSB_TRY(col_norms(Bsrc, n, nrhs, ldbs, nb.as<double>(), bn, s));
   // x0
   FOSB_CUDA(convert_c128_to_c64(Bsrc, n, nrhs, ldbs, d.p, nrhs, s));
-  FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s));
+  FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status));
   FOSB_CUDA(convert_c64_to_c128(d.p, n, nrhs, nrhs, X, ldx, s));
   double prev = INFINITY, prev2 = INFINITY, berr = INFINITY;
   int it = 0;
@@ -121,7 +121,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
     prev2 = prev;
     prev = berr;
     FOSB_CUDA(convert_c128_to_c64(r.p, n, nrhs, nrhs, d.p, nrhs, s));
-    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status));
     FOSB_CUDA(axpy_c64_into_c128(d.p, n, nrhs, nrhs, X, ldx, s));
     ++it;
   }
@@ -129,6 +129,10 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
     stats->iters = it;
     stats->backward_error = berr;
   }
+  int status = 0;  // tensor-core triangular updates report a bounded-wait time-out here
+  FOSB_CUDA(cudaMemcpyAsync(&status, lu->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  if (status == FOSB_ERR_TIMEOUT) return fail(FOSB_ERR_TIMEOUT, "fosb_solve: tensor-core wait timed out");
   if (!(berr <= tol) && !(berr <= 1e-13)) {
     return fail(FOSB_ERR_NOT_CONVERGED, "fosb_solve: refinement stalled at backward error " + std::to_string(berr));
   }

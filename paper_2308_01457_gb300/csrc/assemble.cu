@@ -489,6 +489,7 @@ inline unsigned blocks_for(int64_t n, int bs) { return unsigned((n + bs - 1) / b
 
 cudaError_t launch_assemble_regular(const DevMesh& m, double k, int arith, void* Z, int64_t ldz, cudaStream_t s) {
   dim3 grid(blocks_for(m.nt, 32), blocks_for(m.nt, 8));
+  ProfScope prof("asm_regular", s, 36.0 * (double(m.nt) * double(m.nt) - double(2 * m.ntouch - m.nt)));
   if (arith == FOSB_ASM_FP64) {
     efie_regular_kernel<double, double><<<grid, 256, 0, s>>>(m, k, static_cast<double*>(Z), ldz);
   } else if (arith == FOSB_ASM_FF) {
@@ -502,6 +503,7 @@ cudaError_t launch_assemble_regular(const DevMesh& m, double k, int arith, void*
 cudaError_t launch_assemble_singular(const DevMesh& m, double k, int nss, bool fp32_out, void* Z, int64_t ldz,
                                      cudaStream_t s) {
   if (m.ntouch == 0) return cudaSuccess;
+  ProfScope prof("asm_singular", s, double(m.ntouch));
   if (fp32_out)
     efie_singular_kernel<float><<<unsigned(m.ntouch), 128, 0, s>>>(m, k, nss, static_cast<float*>(Z), ldz);
   else

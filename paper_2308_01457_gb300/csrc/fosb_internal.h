@@ -28,6 +28,24 @@ inline cudaError_t launched(uint64_t n = 1) {
   return cudaGetLastError();
 }
 
+// Kernel-family timing (fosb_profile_enable): RAII scope recording CUDA events around a
+// launch on its stream, with the launch's algorithmic work.
+bool profiling();
+class ProfScope {
+ public:
+  ProfScope(const char* family, cudaStream_t s, double work);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  const char* fam_;
+  cudaStream_t s_;
+  double work_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+  bool active_ = false;
+};
+
 #define FOSB_TRY(call)                    \
   do {                                    \
     fosb_status s_ = (call);              \
@@ -155,7 +173,7 @@ fosb_status getrf_external_scratch(void* A, int64_t n, int64_t lda, int32_t* ipi
                                    int64_t max_ctas, cudaStream_t s);
 template <typename T>
 cudaError_t getrs(const void* LU, int64_t n, int64_t ldlu, const int32_t* ipiv, void* X, int64_t nrhs, int64_t ldx,
-                  cudaStream_t s);
+                  cudaStream_t s, int* status = nullptr);
 cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                 cudaStream_t s);
 cudaError_t convert_c64_to_c128(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,

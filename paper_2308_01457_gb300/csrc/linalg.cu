@@ -972,6 +972,7 @@ cudaError_t launch_panel(typename C2<T>::type* Ap, int64_t m, int jb, int64_t ld
                          PanelScratch* scr, double* cand_val, int64_t* cand_row, typename C2<T>::type* cand_data,
                          typename C2<T>::type* rowj, int* d_status, int64_t G_cap, int nsm, cudaStream_t s) {
   using V = typename C2<T>::type;
+  ProfScope prof("lu_panel", s, 4.0 * double(m) * jb * jb);
   static bool attr[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1092,6 +1093,7 @@ cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, doub
   int64_t k_chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
   splits = (K + k_chunk - 1) / k_chunk;
   dim3 grid(cdiv(N, TBN), cdiv(M, TBM), unsigned(splits));
+  ProfScope prof("gemm_ff", s, 8.0 * double(M) * double(N) * double(K));
   if (splits > 1) {
     if (beta == 0.0) {
       cudaError_t e = cudaMemset2DAsync(c, ldc * sizeof(V), 0, N * sizeof(V), M, s);
@@ -1228,7 +1230,7 @@ template fosb_status getrf_external_scratch<float>(void*, int64_t, int64_t, int3
 // X <- Z^{-1} X given the factors (perm = composed row permutation, device).
 template <typename T>
 cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm, void* Xv, int64_t nrhs, int64_t ldx,
-                  cudaStream_t s) {
+                  cudaStream_t s, int* status) {
   using V = typename C2<T>::type;
   const V* LU = static_cast<const V*>(LUv);
   V* X = static_cast<V*>(Xv);
@@ -1251,8 +1253,12 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
     diag(i0, ib, 0);
     int64_t rest = n - i0 - ib;
     if (rest > 0) {
-      e = gemm<T>(OP_N, OP_N, rest, nrhs, ib, -1.0, 0.0, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0,
-                  tmp + (i0 + ib) * nrhs, nrhs, s);
+      if (sizeof(T) == 4 && status && nrhs >= 16)  // wide right-hand sides: tensor cores
+        e = cgemm_update_tc(rest, nrhs, ib, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs,
+                            tmp + (i0 + ib) * nrhs, nrhs, status, s);
+      else
+        e = gemm<T>(OP_N, OP_N, rest, nrhs, ib, -1.0, 0.0, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs,
+                    1.0, tmp + (i0 + ib) * nrhs, nrhs, s);
       if (e != cudaSuccess) return e;
     }
   }
@@ -1262,7 +1268,10 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
     int ib = int(i1 - i0);
     diag(i0, ib, 1);
     if (i0 > 0) {
-      e = gemm<T>(OP_N, OP_N, i0, nrhs, ib, -1.0, 0.0, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0, tmp, nrhs, s);
+      if (sizeof(T) == 4 && status && nrhs >= 16)
+        e = cgemm_update_tc(i0, nrhs, ib, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, tmp, nrhs, status, s);
+      else
+        e = gemm<T>(OP_N, OP_N, i0, nrhs, ib, -1.0, 0.0, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0, tmp, nrhs, s);
       if (e != cudaSuccess) return e;
     }
   }
@@ -1271,8 +1280,10 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   return cudaGetLastError();
 }
 
-template cudaError_t getrs<double>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t);
-template cudaError_t getrs<float>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t);
+template cudaError_t getrs<double>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t,
+                                   int*);
+template cudaError_t getrs<float>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t,
+                                  int*);
 
 cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                 cudaStream_t s) {

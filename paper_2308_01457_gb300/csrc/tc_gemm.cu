@@ -295,6 +295,7 @@ cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int6
   if (grid.y > 65535u) return cudaErrorInvalidValue;
   // 16-byte epilogue accesses need a 16-byte aligned C with an even leading dimension
   const int vec_ok = (reinterpret_cast<uintptr_t>(C) % 16 == 0) && (ldc % 2 == 0);
+  ProfScope prof("lu_update", s, 8.0 * double(M) * double(N) * double(K));
   cgemm_update_tc_kernel<<<grid, 256, TC_SMEM, s>>>(M, N, K, static_cast<const float2*>(A), lda,
                                                    static_cast<const float2*>(B), ldb, static_cast<float2*>(C), ldc,
                                                    status, vec_ok);

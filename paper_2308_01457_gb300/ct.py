@@ -129,7 +129,7 @@ class FOSBProblem:
             cov_start.record()
         fine = self.levels[self.L]
         F = torch.empty((nd3, 1), dtype=dt, device=dev)
-        farfield_moments(fine.mesh, self.k, self.dirs, fine.u, F)
+        farfield_moments(fine.mesh, self.k, self.dirs, fine.u, F, prec=self.prec)
         cov = torch.empty((nd3, nd3), dtype=dt, device=dev)
         pcov = torch.empty((nd3, nd3), dtype=dt, device=dev) if self.pseudo else None
         first = True
@@ -142,6 +142,7 @@ class FOSBProblem:
                 covariance(a.mesh, a.lu, a.u, c.mesh, c.lu, c.u, self.k, Sig, self.kernel, self.sigma, self.ell,
                            pseudo=pseudo)
                 farfield_moments(a.mesh, self.k, self.dirs, Sig, out, m2=c.mesh, weight=float(sgn), mirror=(l1 != l2),
+                                 prec=self.prec,
                                  pseudo=pseudo, accumulate=not first)
             first = False
         if timers is not None:
