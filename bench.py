@@ -225,6 +225,7 @@ def run_fosb(args):
     # IR quality (refined path must reach FP64 backward error)
     berr = max(prob.levels[l].berr for l in prob.levels)
     e2e = run_e2e(args, W, meshes, dirs, arith) if (rank == 0 and not args.no_e2e) else None
+    fp64 = run_fp64_compare(W, meshes, dirs, out, ms) if (rank == 0 and not args.no_fp64) else None
     if rank != 0:
         return
     line = {
@@ -245,6 +246,7 @@ def run_fosb(args):
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,
+        "fp64": fp64,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
     if not args.no_cpu_baseline:
@@ -252,6 +254,45 @@ def run_fosb(args):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_fp64_compare(W, meshes, dirs, out_mixed, ms_mixed):
+    """One step of the same workload in plain FP64 (FP64 assembly, complex128 LU on the
+    FP64 tensor path, no refinement), outside the timed region: its time, assembly rate
+    and the relative difference of the mixed step's mean far field and CT covariance."""
+    import torch
+
+    import paper_2308_01457_gb300 as F
+    from paper_2308_01457_gb300.ct import FOSBProblem
+
+    prob = FOSBProblem(meshes, W["k"], (0, 0, 1), (1, 0, 0), dirs, W["L0"], W["L"], F.COV_GAUSS, W["sigma"],
+                       W["ell"], prec=F.FP64, arith=F.ASM_FP64).setup()
+    timers = {}
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    Fm, cov = prob.run(timers)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    L = W["L"]
+    NL = prob.levels[L].mesh.n_edges
+    t_asm = sum(x.elapsed_time(y) for x, y in timers[f"assemble_l{L}"])
+
+    def rel(x, y):
+        return float(torch.linalg.norm(x - y) / torch.linalg.norm(y))
+
+    res = {"s_per_step": round(ms / 1e3, 4), "mixed_speedup": round(ms / ms_mixed, 2),
+           "efie_entries_per_s": round(NL * NL / (t_asm * 1e-3), 1),
+           "phase_ms": {"assemble_finest": round(t_asm, 2),
+                        "factor_finest": round(sum(x.elapsed_time(y) for x, y in timers[f"factor_l{L}"]), 2),
+                        "covariance_ct": round(sum(x.elapsed_time(y) for x, y in timers["covariance_ct"]), 2)},
+           "rel_diff_mean_farfield": rel(out_mixed[0], Fm), "rel_diff_ct_covariance": rel(out_mixed[1], cov),
+           "note": "one step, same workload, FP64 assembly and complex128 LU (DMMA), timed with CUDA events"}
+    prob.release()
+    del prob
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_e2e(args, W, meshes, dirs, arith):
@@ -383,6 +424,7 @@ def main():
                     help="regular-pair assembly arithmetic: float-float on the FP32 pipe (default) or FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps

@@ -443,10 +443,14 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(int opB, int64_t M, in
 }
 
 // ------------------------------------------------------------------ panel factorisation
+// Panel scratch header (zeroed before each factorisation): a monotonic arrival counter for
+// the grid barrier and a ring of four 64-bit pivot keys (column c uses key[c & 3]).
 struct PanelScratch {
   unsigned count;
   unsigned gen;
+  unsigned long long key[4];
 };
+static_assert(sizeof(PanelScratch) <= 256, "the panel header must fit the zeroed 256 bytes");
 
 constexpr int kPanelThreads = 256;
 constexpr int kMaxPanelRows = 2048;  // rows per CTA (multipliers kept in shared memory)
@@ -482,110 +486,111 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, i
   return ok != 0;
 }
 
-// cand_val[2][G], cand_row[2][G], cand_data[2][G][jb], rowj[2][jb]
+// Grid barrier on a counter that only grows: every CTA adds one and waits until the count
+// reaches target (this launch's base + (column + 1) x CTAs), so no CTA has to reset it.
+// Bounded: after kSpinLimit polls the status word is set to FOSB_ERR_TIMEOUT and the CTA
+// leaves.
+__device__ bool grid_arrive_wait(unsigned* count, unsigned target, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    volatile unsigned* vc = count;
+    long long spins = 0;
+    while (int(*vc - target) < 0) {
+      if (++spins > kSpinLimit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
+        atomicExch(status, FOSB_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Pivot key: magnitude |Re| + |Im| in the upper 32 bits (float bits for complex64; the top
+// 32 bits of the double for complex128, a monotone truncation), ~row in the lower 32 bits,
+// so the largest key is the largest magnitude with ties going to the lowest row.
+template <typename T>
+__device__ __forceinline__ unsigned long long pivot_key(typename C2<T>::type v, int64_t row) {
+  unsigned hi;
+  if constexpr (sizeof(T) == 4)
+    hi = __float_as_uint(fabsf(v.x) + fabsf(v.y));
+  else
+    hi = unsigned(uint64_t(__double_as_longlong(fabs(v.x) + fabs(v.y))) >> 32);
+  return (static_cast<unsigned long long>(hi) << 32) | (0xFFFFFFFFu - static_cast<unsigned>(row));
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, k, off);
+    k = o > k ? o : k;
+  }
+  return k;
+}
+
+// cand_data[2][G][jb], rowj[2][jb]
+// One column per step over the CTAs' row blocks of the panel (rows [lo, hi) each), in
+// global memory; cand_data[2][G][jb] and rowj[2][jb] carry the candidate rows and row j.
 template <typename T>
 __global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::type* A, int64_t m, int jb, int64_t lda,
                                                               int32_t* ipiv, int64_t row_base, PanelScratch* scr,
-                                                              double* cand_val, int64_t* cand_row,
-                                                              typename C2<T>::type* cand_data,
+                                                              unsigned bar_base, typename C2<T>::type* cand_data,
                                                               typename C2<T>::type* rowj, int* status) {
   using V = typename C2<T>::type;
   const unsigned G = gridDim.x;
   const int64_t chunk = (m + G - 1) / G;
   const int64_t lo = int64_t(blockIdx.x) * chunk, hi = min(m, lo + chunk);
-  __shared__ double s_val[kPanelThreads / 32];
-  __shared__ int64_t s_row[kPanelThreads / 32];
+  __shared__ unsigned long long s_key[kPanelThreads / 32];
   __shared__ V s_l[kMaxPanelRows];
   __shared__ V s_piv[64];
   __shared__ int64_t s_p;
-  __shared__ int s_win;
+#define ROW(r, c) A[(r) * lda + (c)]
   for (int j = 0; j < jb; ++j) {
     const int par = j & 1;
     // 1. local pivot candidate (largest |Re|+|Im|, ties -> lowest row)
-    double best = -1.0;
-    int64_t brow = m;
+    unsigned long long best = 0ull;
     for (int64_t r = max(lo, int64_t(j)) + threadIdx.x; r < hi; r += blockDim.x) {
-      V v = A[r * lda + j];
-      double a = fabs(double(v.x)) + fabs(double(v.y));
-      if (a > best) {
-        best = a;
-        brow = r;
-      }
+      const unsigned long long k = pivot_key<T>(A[r * lda + j], r);
+      best = k > best ? k : best;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffffu, best, off);
-      int64_t orow = __shfl_xor_sync(0xffffffffu, brow, off);
-      if (ob > best || (ob == best && orow < brow)) {
-        best = ob;
-        brow = orow;
-      }
-    }
-    if ((threadIdx.x & 31) == 0) {
-      s_val[threadIdx.x >> 5] = best;
-      s_row[threadIdx.x >> 5] = brow;
-    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0) s_key[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < kPanelThreads / 32; ++w)
-        if (s_val[w] > best || (s_val[w] == best && s_row[w] < brow)) {
-          best = s_val[w];
-          brow = s_row[w];
-        }
-      s_val[0] = best;
-      s_row[0] = brow;
+      for (int w = 1; w < kPanelThreads / 32; ++w) best = s_key[w] > best ? s_key[w] : best;
+      s_key[0] = best;
     }
     __syncthreads();
-    best = s_val[0];
-    brow = s_row[0];
-    // 2. publish the candidate (value, row and its panel row) and, by its owner, row j
-    if (threadIdx.x == 0) {
-      cand_val[par * G + blockIdx.x] = best;
-      cand_row[par * G + blockIdx.x] = brow;
-    }
+    best = s_key[0];
+    const int64_t brow = best != 0ull ? int64_t(0xFFFFFFFFu - unsigned(best & 0xFFFFFFFFull)) : m;
+    // 2. publish the candidate's panel row (and, by its owner, row j); fold the key into
+    //    this column's slot; wait for every CTA
     for (int c = threadIdx.x; c < jb; c += blockDim.x) {
-      cand_data[(int64_t(par) * G + blockIdx.x) * jb + c] = (brow < m) ? A[brow * lda + c] : V{T(0), T(0)};
-      if (j >= lo && j < hi) rowj[par * jb + c] = A[int64_t(j) * lda + c];
+      cand_data[(int64_t(par) * G + blockIdx.x) * jb + c] = (brow < m) ? ROW(brow, c) : V{T(0), T(0)};
+      if (j >= lo && j < hi) rowj[par * jb + c] = ROW(int64_t(j), c);
     }
+    if (threadIdx.x == 0 && best != 0ull) atomicMax(&scr->key[(row_base + j) & 3], best);
     __threadfence();
-    if (!grid_barrier(&scr->count, &scr->gen, G, status)) return;
-    // 3. global pivot: every CTA reduces the G candidates identically
-    if (threadIdx.x < 32) {
-      double b = -1.0;
-      int64_t r = m;
-      int win = 0;
-      for (unsigned g = threadIdx.x; g < G; g += 32) {
-        double v = ((volatile double*)cand_val)[par * G + g];
-        int64_t rr = ((volatile int64_t*)cand_row)[par * G + g];
-        if (v > b || (v == b && rr < r)) {
-          b = v;
-          r = rr;
-          win = int(g);
-        }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, b, off);
-        int64_t orow = __shfl_xor_sync(0xffffffffu, r, off);
-        int ow = __shfl_xor_sync(0xffffffffu, win, off);
-        if (ob > b || (ob == b && orow < r)) {
-          b = ob;
-          r = orow;
-          win = ow;
-        }
-      }
-      if (threadIdx.x == 0) {
-        s_p = r;
-        s_win = win;
-        if (blockIdx.x == 0) {
-          ipiv[j] = int32_t(row_base + r);
-          if (!(b > 0.0)) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
-        }
+    if (!grid_arrive_wait(&scr->count, bar_base + unsigned(j + 1) * G, status)) return;
+    // 3. the winning key names the pivot row and, through the row partition, its CTA
+    if (threadIdx.x == 0) {
+      const unsigned long long key = *reinterpret_cast<volatile unsigned long long*>(&scr->key[(row_base + j) & 3]);
+      s_p = int64_t(0xFFFFFFFFu - unsigned(key & 0xFFFFFFFFull));
+      if (blockIdx.x == 0) {
+        ipiv[j] = int32_t(row_base + s_p);
+        if ((key >> 32) == 0ull) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
+        scr->key[(row_base + j + 3) & 3] = 0ull;  // previous column's slot: every CTA has read it
       }
     }
     __syncthreads();
     const int64_t p = s_p;
-    const V* pdata = cand_data + (int64_t(par) * G + s_win) * jb;
+    const V* pdata = cand_data + (int64_t(par) * G + p / chunk) * jb;
     for (int c = threadIdx.x; c < jb; c += blockDim.x) s_piv[c] = __ldcg(pdata + c);
     __syncthreads();
     // 4. swap rows j and p inside the panel
@@ -622,6 +627,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::ty
     }
     __syncthreads();
   }
+#undef ROW
 }
 
 // The same panel factorisation with each CTA's row block resident in shared memory
@@ -630,8 +636,8 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::ty
 template <typename T>
 __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(typename C2<T>::type* A, int64_t m, int jb,
                                                                    int64_t lda, int32_t* ipiv, int64_t row_base,
-                                                                   PanelScratch* scr, double* cand_val,
-                                                                   int64_t* cand_row, typename C2<T>::type* cand_data,
+                                                                   PanelScratch* scr, unsigned bar_base,
+                                                                   typename C2<T>::type* cand_data,
                                                                    typename C2<T>::type* rowj, int* status) {
   using V = typename C2<T>::type;
   extern __shared__ unsigned char panel_raw[];
@@ -640,94 +646,51 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(typename C2<T
   const int64_t chunk = (m + G - 1) / G;
   const int64_t lo = int64_t(blockIdx.x) * chunk, hi = min(m, lo + chunk);
   const int nr = hi > lo ? int(hi - lo) : 0;
-  __shared__ double s_val[kPanelThreads / 32];
-  __shared__ int64_t s_row[kPanelThreads / 32];
+  __shared__ unsigned long long s_key[kPanelThreads / 32];
   __shared__ V s_piv[64];
   __shared__ int64_t s_p;
-  __shared__ int s_win;
   for (int e = threadIdx.x; e < nr * jb; e += blockDim.x) sP[e] = A[(lo + e / jb) * lda + e % jb];
   __syncthreads();
+#define ROW(r, c) sP[((r) - lo) * jb + (c)]
   for (int j = 0; j < jb; ++j) {
     const int par = j & 1;
-    double best = -1.0;
-    int64_t brow = m;
+    unsigned long long best = 0ull;
     for (int r = (j > lo ? int(j - lo) : 0) + threadIdx.x; r < nr; r += blockDim.x) {
-      V v = sP[r * jb + j];
-      double a = fabs(double(v.x)) + fabs(double(v.y));
-      if (a > best) {
-        best = a;
-        brow = lo + r;
-      }
+      const unsigned long long k = pivot_key<T>(sP[r * jb + j], lo + r);
+      best = k > best ? k : best;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffffu, best, off);
-      int64_t orow = __shfl_xor_sync(0xffffffffu, brow, off);
-      if (ob > best || (ob == best && orow < brow)) {
-        best = ob;
-        brow = orow;
-      }
-    }
-    if ((threadIdx.x & 31) == 0) {
-      s_val[threadIdx.x >> 5] = best;
-      s_row[threadIdx.x >> 5] = brow;
-    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0) s_key[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < kPanelThreads / 32; ++w)
-        if (s_val[w] > best || (s_val[w] == best && s_row[w] < brow)) {
-          best = s_val[w];
-          brow = s_row[w];
-        }
-      s_val[0] = best;
-      s_row[0] = brow;
-      cand_val[par * G + blockIdx.x] = best;
-      cand_row[par * G + blockIdx.x] = brow;
+      for (int w = 1; w < kPanelThreads / 32; ++w) best = s_key[w] > best ? s_key[w] : best;
+      s_key[0] = best;
     }
     __syncthreads();
-    brow = s_row[0];
+    best = s_key[0];
+    const int64_t brow = best != 0ull ? int64_t(0xFFFFFFFFu - unsigned(best & 0xFFFFFFFFull)) : m;
+    // 2. publish the candidate's panel row (and, by its owner, row j); fold the key into
+    //    this column's slot; wait for every CTA
     for (int c = threadIdx.x; c < jb; c += blockDim.x) {
-      cand_data[(int64_t(par) * G + blockIdx.x) * jb + c] = (brow < m) ? sP[(brow - lo) * jb + c] : V{T(0), T(0)};
-      if (j >= lo && j < hi) rowj[par * jb + c] = sP[(j - lo) * jb + c];
+      cand_data[(int64_t(par) * G + blockIdx.x) * jb + c] = (brow < m) ? ROW(brow, c) : V{T(0), T(0)};
+      if (j >= lo && j < hi) rowj[par * jb + c] = ROW(int64_t(j), c);
     }
+    if (threadIdx.x == 0 && best != 0ull) atomicMax(&scr->key[(row_base + j) & 3], best);
     __threadfence();
-    if (!grid_barrier(&scr->count, &scr->gen, G, status)) return;
-    if (threadIdx.x < 32) {
-      double b = -1.0;
-      int64_t r = m;
-      int win = 0;
-      for (unsigned g = threadIdx.x; g < G; g += 32) {
-        double v = ((volatile double*)cand_val)[par * G + g];
-        int64_t rr = ((volatile int64_t*)cand_row)[par * G + g];
-        if (v > b || (v == b && rr < r)) {
-          b = v;
-          r = rr;
-          win = int(g);
-        }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, b, off);
-        int64_t orow = __shfl_xor_sync(0xffffffffu, r, off);
-        int ow = __shfl_xor_sync(0xffffffffu, win, off);
-        if (ob > b || (ob == b && orow < r)) {
-          b = ob;
-          r = orow;
-          win = ow;
-        }
-      }
-      if (threadIdx.x == 0) {
-        s_p = r;
-        s_win = win;
-        if (blockIdx.x == 0) {
-          ipiv[j] = int32_t(row_base + r);
-          if (!(b > 0.0)) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
-        }
+    if (!grid_arrive_wait(&scr->count, bar_base + unsigned(j + 1) * G, status)) return;
+    // 3. the winning key names the pivot row and, through the row partition, its CTA
+    if (threadIdx.x == 0) {
+      const unsigned long long key = *reinterpret_cast<volatile unsigned long long*>(&scr->key[(row_base + j) & 3]);
+      s_p = int64_t(0xFFFFFFFFu - unsigned(key & 0xFFFFFFFFull));
+      if (blockIdx.x == 0) {
+        ipiv[j] = int32_t(row_base + s_p);
+        if ((key >> 32) == 0ull) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
+        scr->key[(row_base + j + 3) & 3] = 0ull;  // previous column's slot: every CTA has read it
       }
     }
     __syncthreads();
     const int64_t p = s_p;
-    const V* pdata = cand_data + (int64_t(par) * G + s_win) * jb;
+    const V* pdata = cand_data + (int64_t(par) * G + p / chunk) * jb;
     for (int c = threadIdx.x; c < jb; c += blockDim.x) s_piv[c] = __ldcg(pdata + c);
     __syncthreads();
     if (p != j) {
@@ -757,6 +720,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(typename C2<T
     }
     __syncthreads();
   }
+#undef ROW
   for (int e = threadIdx.x; e < nr * jb; e += blockDim.x) A[(lo + e / jb) * lda + e % jb] = sP[e];
 }
 
@@ -969,7 +933,7 @@ constexpr int kPanelSmemBudget = 200 * 1024;
 
 template <typename T>
 cudaError_t launch_panel(typename C2<T>::type* Ap, int64_t m, int jb, int64_t lda, int32_t* ip, int64_t row_base,
-                         PanelScratch* scr, double* cand_val, int64_t* cand_row, typename C2<T>::type* cand_data,
+                         PanelScratch* scr, unsigned& arrivals, typename C2<T>::type* cand_data,
                          typename C2<T>::type* rowj, int* d_status, int64_t G_cap, int nsm, cudaStream_t s) {
   using V = typename C2<T>::type;
   ProfScope prof("lu_panel", s, 4.0 * double(m) * jb * jb);
@@ -990,15 +954,21 @@ cudaError_t launch_panel(typename C2<T>::type* Ap, int64_t m, int jb, int64_t ld
   if (chunk <= rows_cap &&
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_smem_kernel<T>, kPanelThreads, smem) == cudaSuccess &&
       per_sm >= 1 && G <= int64_t(per_sm) * nsm) {
-    void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_smem_kernel<T>), dim3(unsigned(G)),
-                                       dim3(kPanelThreads), args, smem, s);
+    unsigned bar_base = arrivals;
+    void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &bar_base, &cand_data, &rowj, &d_status};
+    cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_smem_kernel<T>), dim3(unsigned(G)),
+                                                dim3(kPanelThreads), args, smem, s);
+    arrivals += unsigned(G) * unsigned(jb);  // every CTA arrives once per column
+    return e;
   }
   G = std::min<int64_t>(std::min<int64_t>(G_cap, nsm), std::max<int64_t>(1, (m + 255) / 256));
   if ((m + G - 1) / G > kMaxPanelRows) return cudaErrorInvalidValue;
-  void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &cand_val, &cand_row, &cand_data, &rowj, &d_status};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)), dim3(kPanelThreads),
-                                     args, 0, s);
+  unsigned bar_base = arrivals;
+  void* args[] = {&Ap, &m, &jb, &lda, &ip, &row_base, &scr, &bar_base, &cand_data, &rowj, &d_status};
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(panel_kernel<T>), dim3(unsigned(G)),
+                                              dim3(kPanelThreads), args, 0, s);
+  arrivals += unsigned(G) * unsigned(jb);
+  return e;
 }
 
 }  // namespace
@@ -1122,48 +1092,84 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
   FOSB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel<T>, kPanelThreads, 0));
   if (per_sm < 1) return fail(FOSB_ERR_CUDA, "getrf: panel kernel cannot be resident");
   const int gmax = nsm * per_sm;
-  // scratch: barrier + candidates
+  // scratch: barrier/key header + candidate rows + row j (double-buffered)
   size_t G_cap = size_t(std::min<int64_t>(gmax, std::max<int64_t>(1, (n + 63) / 64)));
-  size_t bytes = 256 + 2 * G_cap * (sizeof(double) + sizeof(int64_t)) + 2 * G_cap * nb * sizeof(V) + 2 * nb * sizeof(V);
+  size_t bytes = 256 + 2 * G_cap * nb * sizeof(V) + 2 * nb * sizeof(V);
   char* scratch = nullptr;
   FOSB_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s));
   FOSB_CUDA(cudaMemsetAsync(scratch, 0, 256, s));
   PanelScratch* scr = reinterpret_cast<PanelScratch*>(scratch);
-  double* cand_val = reinterpret_cast<double*>(scratch + 256);
-  int64_t* cand_row = reinterpret_cast<int64_t*>(cand_val + 2 * G_cap);
-  V* cand_data = reinterpret_cast<V*>(cand_row + 2 * G_cap);
+  V* cand_data = reinterpret_cast<V*>(scratch + 256);
   V* rowj = cand_data + 2 * G_cap * nb;
+  unsigned arrivals = 0;  // grid-barrier arrivals so far (the counter starts at zero)
   fosb_status st = FOSB_OK;
-  for (int64_t j0 = 0; j0 < n && st == FOSB_OK; j0 += nb) {
-    int jb = int(std::min<int64_t>(nb, n - j0));
-    int64_t m = n - j0;
-    V* Ap = A + j0 * lda + j0;
-    int32_t* ip = ipiv + j0;
-    cudaError_t e = launch_panel<T>(Ap, m, jb, lda, ip, j0, scr, cand_val, cand_row, cand_data, rowj, d_status,
-                                    int64_t(G_cap), nsm, s);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "getrf: cooperative panel launch");
-      break;
-    }
+  // one 64-column panel at column j0: cooperative factorisation + row swaps elsewhere
+  auto panel_step = [&](int64_t j0, int jb) -> cudaError_t {
+    cudaError_t e = launch_panel<T>(A + j0 * lda + j0, n - j0, jb, lda, ipiv + j0, j0, scr, arrivals,
+                                    cand_data, rowj, d_status, int64_t(G_cap), nsm, s);
+    if (e != cudaSuccess) return e;
     laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
     note_launches(2);  // panel + row swaps
-    int64_t rest = n - j0 - jb;
-    if (rest > 0) {
-      enable_trsv_smem<T>();
-      trsv_warp_kernel<T><<<cdiv(rest, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
-      note_launches(1);
-      if constexpr (sizeof(T) == 4)  // complex64 factors: tensor cores (tcgen05, 3xTF32)
-        e = cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s);
-      else
-        e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0, Ap + jb * lda + jb,
-                    lda, s);
+    return cudaGetLastError();
+  };
+  // X (jb rows x ncols, ld lda) := L^{-1} X with L the unit lower jb x jb block at D
+  auto trsm_lower = [&](const V* D, int jb, V* X, int64_t ncols) -> cudaError_t {
+    enable_trsv_smem<T>();
+    trsv_warp_kernel<T><<<cdiv(ncols, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(D, lda, jb, 0, X, lda, ncols);
+    return launched();
+  };
+  if constexpr (sizeof(T) == 4) {
+    // complex64 factors: outer blocks of 128 columns, each factored as two 64-column
+    // panels, so that the tensor-core trailing update runs with K = 128 and streams the
+    // trailing matrix half as often as 64-column blocking would.
+    const int64_t NB = 128;
+    for (int64_t j0 = 0; j0 < n && st == FOSB_OK; j0 += NB) {
+      const int jb = int(std::min<int64_t>(NB, n - j0));
+      const int jb1 = std::min(jb, nb), jb2 = jb - jb1;
+      V* Ap = A + j0 * lda + j0;
+      cudaError_t e = panel_step(j0, jb1);
+      if (e == cudaSuccess && jb2 > 0) {
+        // right half of the block: U rows of the first panel, then its rank-64 update
+        e = trsm_lower(Ap, jb1, Ap + jb1, jb2);
+        if (e == cudaSuccess)
+          e = cgemm_update_tc(n - j0 - jb1, jb2, jb1, Ap + jb1 * lda, lda, Ap + jb1, lda, Ap + jb1 * lda + jb1, lda,
+                              d_status, s);
+        if (e == cudaSuccess) e = panel_step(j0 + jb1, jb2);
+      }
+      const int64_t rest = n - j0 - jb;
+      if (e == cudaSuccess && rest > 0) {
+        // U12 = L11^{-1} A12 for the 128-row block (two 64-row sweeps and the coupling update)
+        e = trsm_lower(Ap, jb1, Ap + jb, rest);
+        if (e == cudaSuccess && jb2 > 0)
+          e = cgemm_update_tc(jb2, rest, jb1, Ap + jb1 * lda, lda, Ap + jb, lda, Ap + jb1 * lda + jb, lda, d_status,
+                              s);
+        if (e == cudaSuccess && jb2 > 0) e = trsm_lower(Ap + jb1 * lda + jb1, jb2, Ap + jb1 * lda + jb, rest);
+        if (e == cudaSuccess)
+          e = cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s);
+      }
+      if (e != cudaSuccess) st = cuda_fail(e, "getrf: blocked step");
+    }
+  } else {
+    for (int64_t j0 = 0; j0 < n && st == FOSB_OK; j0 += nb) {
+      int jb = int(std::min<int64_t>(nb, n - j0));
+      V* Ap = A + j0 * lda + j0;
+      cudaError_t e = panel_step(j0, jb);
       if (e != cudaSuccess) {
-        st = cuda_fail(e, "getrf: trailing update");
+        st = cuda_fail(e, "getrf: cooperative panel launch");
         break;
       }
+      int64_t rest = n - j0 - jb;
+      if (rest > 0) {
+        e = trsm_lower(Ap, jb, Ap + jb, rest);
+        if (e == cudaSuccess)
+          e = gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0,
+                      Ap + jb * lda + jb, lda, s);
+        if (e != cudaSuccess) {
+          st = cuda_fail(e, "getrf: trailing update");
+          break;
+        }
+      }
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_fail(e, "getrf");
   }
   cudaFreeAsync(scratch, s);
   return st;
@@ -1174,7 +1180,7 @@ template fosb_status getrf<float>(void*, int64_t, int64_t, int32_t*, int*, cudaS
 
 size_t getrf_scratch_bytes(int64_t max_ctas, bool c128) {
   const size_t v = c128 ? 16 : 8, nb = 64;
-  return 256 + 2 * size_t(max_ctas) * (sizeof(double) + sizeof(int64_t)) + 2 * size_t(max_ctas) * nb * v + 2 * nb * v;
+  return 256 + 2 * size_t(max_ctas) * nb * v + 2 * nb * v;
 }
 
 // The same blocked factorisation as getrf, with the panel kernel's scratch (barrier
@@ -1194,16 +1200,15 @@ fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ip
   const int64_t G_cap = std::min<int64_t>(int64_t(nsm) * per_sm, max_ctas);
   char* base = static_cast<char*>(scratch);
   PanelScratch* scr = reinterpret_cast<PanelScratch*>(base);
-  double* cand_val = reinterpret_cast<double*>(base + 256);
-  int64_t* cand_row = reinterpret_cast<int64_t*>(cand_val + 2 * max_ctas);
-  V* cand_data = reinterpret_cast<V*>(cand_row + 2 * max_ctas);
+  V* cand_data = reinterpret_cast<V*>(base + 256);
   V* rowj = cand_data + 2 * max_ctas * nb;
+  unsigned arrivals = 0;
   for (int64_t j0 = 0; j0 < n; j0 += nb) {
     int jb = int(std::min<int64_t>(nb, n - j0));
     int64_t m = n - j0;
     V* Ap = A + j0 * lda + j0;
     int32_t* ip = ipiv + j0;
-    FOSB_CUDA(launch_panel<T>(Ap, m, jb, lda, ip, j0, scr, cand_val, cand_row, cand_data, rowj, d_status, G_cap, nsm, s));
+    FOSB_CUDA(launch_panel<T>(Ap, m, jb, lda, ip, j0, scr, arrivals, cand_data, rowj, d_status, G_cap, nsm, s));
     laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
     note_launches(2);
     int64_t rest = n - j0 - jb;
