@@ -107,7 +107,8 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   int it = 0;
   for (;;) {
     FOSB_CUDA(copy_matrix(Bsrc, n, nrhs, ldbs, r.p, nrhs, 16, s));
-    FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s));
+    FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s,
+                           lu->zff));
     FOSB_TRY(col_norms(r.p, n, nrhs, nrhs, nb.as<double>(), rn, s));
     FOSB_TRY(col_norms(X, n, nrhs, ldx, nb.as<double>(), xn, s));
     berr = 0.0;
@@ -215,6 +216,10 @@ fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu
   if (prec == FOSB_MIXED) {
     lu->zref = Z;
     lu->ldz = ldz;
+    // the residual GEMMs read Z as (hi, lo) float pairs: split it once here (n x n float4)
+    if ((e = cudaMalloc(&lu->zff, sizeof(float) * 4 * n * n)) != cudaSuccess ||
+        (e = split_ff(Z, n, n, ldz, lu->zff, n, s)) != cudaSuccess)
+      return cleanup(cuda_fail(e, "fosb_factor: split copy of Z"));
     Scratch nrm(s);
     if ((e = nrm.alloc(sizeof(double))) != cudaSuccess || (e = norm_inf_c128(Z, n, n, ldz, nrm.as<double>(), s)) ||
         (e = cudaMemcpyAsync(&lu->znorm_inf, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s)))
@@ -266,6 +271,7 @@ fosb_status fosb_lu_destroy(fosb_lu lu) {
   if (lu->lu) cudaFree(lu->lu);
   if (lu->ipiv) cudaFree(lu->ipiv);
   if (lu->d_status) cudaFree(lu->d_status);
+  if (lu->zff) cudaFree(lu->zff);
   delete lu;
   return FOSB_OK;
 }
@@ -309,9 +315,10 @@ fosb_status fosb_covariance(fosb_mesh m1, fosb_lu lu1, const void* u1, fosb_mesh
   cudaError_t e;
   if (c64)
     e = gemm<float>(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
+  else if (prec == FOSB_MIXED)
+    e = gemm_c128_ff(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
   else
-    e = (prec == FOSB_MIXED ? gemm_c128_ff : gemm<double>)(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p,
-                                                           r, y2.p, r, 0.0, Sigma, lds, s);
+    e = gemm<double>(OP_N, pseudo ? OP_T : OP_C, d1.ne, d2.ne, r, 1.0, 0.0, y1.p, r, y2.p, r, 0.0, Sigma, lds, s);
   FOSB_CUDA(e);
   return FOSB_OK;
 }

@@ -105,6 +105,7 @@ struct fosb_lu_s {
   int32_t* ipiv = nullptr;     // n pivots (row swapped with i at step i), device
   const void* zref = nullptr;  // MIXED: non-owning complex128 Z for residuals
   int64_t ldz = 0;
+  void* zff = nullptr;         // MIXED: (hi, lo) float split of Z (n x n float4) for the residual GEMMs
   double znorm_inf = 0.0;      // ||Z||_inf (FP64)
   int* d_status = nullptr;     // device status word
 };
@@ -161,13 +162,23 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
 // a bounded mbarrier wait that gives up sets *status = FOSB_ERR_TIMEOUT
 cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                             void* C, int64_t ldc, int* status, cudaStream_t s);
-// complex128 GEMM computed in float-float on the FP32 pipe (FP64-class accuracy)
+// complex128 GEMM computed in float-float on the FP32 pipe (FP64-class accuracy).  A_split,
+// if given, is split_ff of A as stored (same shape, leading dimension lda).
 cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im,
                          const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
-                         cudaStream_t s);
+                         cudaStream_t s, const void* A_split = nullptr);
+// dst (rows x cols float4, ldd) = (hi, lo) float split of the complex128 src
+cudaError_t split_ff(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                     cudaStream_t s);
 template <typename T>
 fosb_status getrf(void* A, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, cudaStream_t s);
 size_t getrf_scratch_bytes(int64_t max_ctas, bool c128);
+// Tournament-pivoting factorisation of one complex64 panel (m x jb at Ap, jb <= 64, m >= jb)
+// with scratch of tslu_scratch_bytes(n_max) bytes (n_max >= m); writes ipiv[0..jb) as
+// absolute rows (row_base + panel row) and permutes the panel's own rows.
+size_t tslu_scratch_bytes(int64_t n_max);
+cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, int64_t row_base, void* scratch,
+                       int64_t n_max, int* d_status, cudaStream_t s);
 template <typename T>
 fosb_status getrf_external_scratch(void* A, int64_t n, int64_t lda, int32_t* ipiv, int* d_status, void* scratch,
                                    int64_t max_ctas, cudaStream_t s);

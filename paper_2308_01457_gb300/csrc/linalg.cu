@@ -279,16 +279,13 @@ __global__ void __launch_bounds__(256, 2) zgemm_dmma_kernel(int opA, int opB, in
 }
 
 // ------------------------------------------------------------------ float-float complex GEMM
-// FP64-class products on the FP32 pipe: complex128 operands are split on load into
-// (hi, lo) float pairs, every real product is formed exactly with an FMA two-product,
-// accumulated with a two-sum, and the (hi, lo) accumulators are renormalised after each
-// k-tile so the low word never grows.  About 48 FP32 instructions per complex MAC
-// against ~1 TFLOP/s of FP64 throughput on this part.  Split-K with FP64 atomics as in
-// the DMMA kernel.
-__device__ __forceinline__ float4 split_c128(double2 v, double sy) {
-  float rh = float(v.x), ih = float(sy * v.y);
-  return make_float4(rh, float(v.x - double(rh)), ih, float(sy * v.y - double(ih)));
-}
+// FP64-class products on the FP32 pipe.  Operands arrive split into (hi, lo) float pairs,
+// float4 (re.hi, re.lo, im.hi, im.lo) per complex128 element (split_ff_kernel, once per
+// element rather than once per tile that reads it); every real product is formed exactly
+// with an FMA two-product, accumulated with a two-sum, and the (hi, lo) accumulators are
+// renormalised after each k-tile so the low word never grows.  About 44 FP32 instructions
+// per complex MAC against ~1 TFLOP/s of FP64 throughput on this part.  Split-K with FP64
+// atomics as in the DMMA kernel.
 __device__ __forceinline__ void ff_acc(float& h, float& l, float xh, float xl, float yh, float yl) {
   float p = xh * yh;
   float e = fmaf(xh, yh, -p);
@@ -299,23 +296,36 @@ __device__ __forceinline__ void ff_acc(float& h, float& l, float xh, float xl, f
   h = s;
 }
 
-template <bool ATOMIC>
+__global__ void split_ff_kernel(const double2* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                                float4* __restrict__ dst, int64_t ldd) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t i = e / cols, j = e % cols;
+  const double2 v = src[i * lds + j];
+  const float rh = float(v.x), ih = float(v.y);
+  dst[i * ldd + j] = make_float4(rh, float(v.x - double(rh)), ih, float(v.y - double(ih)));
+}
+
+// NJ complex columns per thread: tile 64 x 16 NJ (NJ = 4, or 3 for 33..48 right-hand sides)
+template <bool ATOMIC, int NJ>
 __global__ void __launch_bounds__(256) zgemm_ff_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, double ar,
-                                                       double ai, const double2* __restrict__ A, int64_t lda,
-                                                       const double2* __restrict__ B, int64_t ldb, double beta,
+                                                       double ai, const float4* __restrict__ A, int64_t lda,
+                                                       const float4* __restrict__ B, int64_t ldb, double beta,
                                                        double2* __restrict__ C, int64_t ldc, int64_t k_chunk) {
   __shared__ float4 As[TBK * 2][TBM + 1];
-  __shared__ float4 Bs[TBK * 2][TBN + 1];
+  constexpr int TN = 16 * NJ;
+  __shared__ float4 Bs[TBK * 2][TN + 1];
   constexpr int KT = TBK * 2;  // 16
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t row0 = int64_t(blockIdx.y) * TBM, col0 = int64_t(blockIdx.x) * TBN;
+  const int64_t row0 = int64_t(blockIdx.y) * TBM, col0 = int64_t(blockIdx.x) * TN;
   const int64_t k_begin = int64_t(blockIdx.z) * k_chunk, k_end = min(K, k_begin + k_chunk);
-  const double sa = opA == OP_C ? -1.0 : 1.0, sb = opB == OP_C ? -1.0 : 1.0;
-  float4 acc[4][4];
+  const float sa = opA == OP_C ? -1.f : 1.f, sb = opB == OP_C ? -1.f : 1.f;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 acc[4][NJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < NJ; ++j) acc[i][j] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t k0 = k_begin; k0 < k_end; k0 += KT) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) {  // A tile 64 x 16
@@ -323,30 +333,34 @@ __global__ void __launch_bounds__(256) zgemm_ff_kernel(int opA, int opB, int64_t
       int r = (opA == OP_N) ? e / KT : e % TBM;
       int kk = (opA == OP_N) ? e % KT : e / TBM;
       int64_t gr = row0 + r, gk = k0 + kk;
-      double2 v = (gr < M && gk < k_end) ? (opA == OP_N ? A[gr * lda + gk] : A[gk * lda + gr]) : make_double2(0.0, 0.0);
-      As[kk][r] = split_c128(v, sa);
+      float4 v = (gr < M && gk < k_end) ? (opA == OP_N ? A[gr * lda + gk] : A[gk * lda + gr]) : z4;
+      v.z *= sa;
+      v.w *= sa;
+      As[kk][r] = v;
     }
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {  // B tile 16 x 64
+    for (int l = 0; l < NJ; ++l) {  // B tile 16 x TN
       int e = tid + 256 * l;
-      int c = (opB == OP_N) ? e % TBN : e / KT;
-      int kk = (opB == OP_N) ? e / TBN : e % KT;
+      int c = (opB == OP_N) ? e % TN : e / KT;
+      int kk = (opB == OP_N) ? e / TN : e % KT;
       int64_t gc = col0 + c, gk = k0 + kk;
-      double2 v = (gc < N && gk < k_end) ? (opB == OP_N ? B[gk * ldb + gc] : B[gc * ldb + gk]) : make_double2(0.0, 0.0);
-      Bs[kk][c] = split_c128(v, sb);
+      float4 v = (gc < N && gk < k_end) ? (opB == OP_N ? B[gk * ldb + gc] : B[gc * ldb + gk]) : z4;
+      v.z *= sb;
+      v.w *= sb;
+      Bs[kk][c] = v;
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < KT; ++kk) {
-      float4 a[4], b[4];
+      float4 a[4], b[NJ];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < NJ; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < NJ; ++j) {
           float4& c = acc[i][j];  // (re.h, re.l, im.h, im.l)
           ff_acc(c.x, c.y, a[i].x, a[i].y, b[j].x, b[j].y);
           ff_acc(c.x, c.y, -a[i].z, -a[i].w, b[j].z, b[j].w);
@@ -357,7 +371,7 @@ __global__ void __launch_bounds__(256) zgemm_ff_kernel(int opA, int opB, int64_t
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {  // renormalise (fast two-sum)
+      for (int j = 0; j < NJ; ++j) {  // renormalise (fast two-sum)
         float4& c = acc[i][j];
         float s = c.x + c.y;
         c.y = c.y - (s - c.x);
@@ -373,7 +387,7 @@ __global__ void __launch_bounds__(256) zgemm_ff_kernel(int opA, int opB, int64_t
     int64_t r = row0 + ty + 16 * i;
     if (r >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NJ; ++j) {
       int64_t c = col0 + tx + 16 * j;
       if (c >= N) continue;
       double xr = double(acc[i][j].x) + double(acc[i][j].y), xi = double(acc[i][j].z) + double(acc[i][j].w);
@@ -1043,9 +1057,17 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
 template cudaError_t gemm<double>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
                                   const void*, int64_t, double, void*, int64_t, cudaStream_t);
 
+cudaError_t split_ff(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                     cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  split_ff_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const double2*>(src), rows, cols, lds,
+                                                         static_cast<float4*>(dst), ldd);
+  return launched();
+}
+
 cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im,
                          const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
-                         cudaStream_t s) {
+                         cudaStream_t s, const void* A_split) {
   using V = double2;
   if (M <= 0 || N <= 0) return cudaSuccess;
   // up to 8 right-hand sides: the FP64 row-per-warp kernel streams A once and is faster
@@ -1053,29 +1075,47 @@ cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, doub
   if (K <= 0 || (opA == OP_N && N <= 8))
     return gemm<double>(opA, opB, M, N, K, alpha_re, alpha_im, A, lda, B, ldb, beta, C, ldc, s);
   if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
-  const V* a = static_cast<const V*>(A);
-  const V* b = static_cast<const V*>(B);
   V* c = static_cast<V*>(C);
-  const int64_t tiles = int64_t(cdiv(N, TBN)) * cdiv(M, TBM);
-  int64_t splits = 1;
-  if ((beta == 0.0 || beta == 1.0) && tiles < 4 * 152 && K >= 1024)
-    splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 512);
-  int64_t k_chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
-  splits = (K + k_chunk - 1) / k_chunk;
-  dim3 grid(cdiv(N, TBN), cdiv(M, TBM), unsigned(splits));
-  ProfScope prof("gemm_ff", s, 8.0 * double(M) * double(N) * double(K));
-  if (splits > 1) {
-    if (beta == 0.0) {
-      cudaError_t e = cudaMemset2DAsync(c, ldc * sizeof(V), 0, N * sizeof(V), M, s);
-      if (e != cudaSuccess) return e;
-    }
-    zgemm_ff_kernel<true><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c, ldc,
-                                               k_chunk);
-  } else {
-    zgemm_ff_kernel<false><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a, lda, b, ldb, beta, c, ldc,
-                                                k_chunk);
+  // (hi, lo) splits of the operands as stored (A_split: a cached split of A with ld = lda)
+  const int64_t ar = opA == OP_N ? M : K, ac = opA == OP_N ? K : M;
+  const int64_t br = opB == OP_N ? K : N, bc = opB == OP_N ? N : K;
+  float4 *as = nullptr, *bs = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&bs), size_t(br * bc) * sizeof(float4), s);
+  if (e == cudaSuccess) e = split_ff(B, br, bc, ldb, bs, bc, s);
+  if (e == cudaSuccess && !A_split) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&as), size_t(ar * ac) * sizeof(float4), s);
+    if (e == cudaSuccess) e = split_ff(A, ar, ac, lda, as, ac, s);
   }
-  return launched();
+  const float4* a4 = A_split ? static_cast<const float4*>(A_split) : as;
+  const int64_t lda4 = A_split ? lda : ac;
+  if (e == cudaSuccess) {
+    const bool n48 = N > 32 && N <= 48;  // 48-wide tiles: less padding for 33..48 columns
+    const int64_t tn = n48 ? 48 : TBN;
+    const int64_t tiles = int64_t(cdiv(N, tn)) * cdiv(M, TBM);
+    int64_t splits = 1;
+    if ((beta == 0.0 || beta == 1.0) && tiles < 4 * 152 && K >= 1024)
+      splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 512);
+    int64_t k_chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+    splits = (K + k_chunk - 1) / k_chunk;
+    dim3 grid(cdiv(N, tn), cdiv(M, TBM), unsigned(splits));
+    ProfScope prof("gemm_ff", s, 8.0 * double(M) * double(N) * double(K));
+    if (splits > 1 && beta == 0.0) e = cudaMemset2DAsync(c, ldc * sizeof(V), 0, N * sizeof(V), M, s);
+#define FOSB_FF(AT, NJ)                                                                                            \
+  zgemm_ff_kernel<AT, NJ><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha_re, alpha_im, a4, lda4, bs, bc, beta, c, ldc, \
+                                               k_chunk)
+    if (e == cudaSuccess) {
+      if (splits > 1) {
+        if (n48) FOSB_FF(true, 3); else FOSB_FF(true, 4);
+      } else {
+        if (n48) FOSB_FF(false, 3); else FOSB_FF(false, 4);
+      }
+    }
+#undef FOSB_FF
+    if (e == cudaSuccess) e = launched();
+  }
+  if (as) cudaFreeAsync(as, s);
+  if (bs) cudaFreeAsync(bs, s);
+  return e;
 }
 template cudaError_t gemm<float>(int, int, int64_t, int64_t, int64_t, double, double, const void*, int64_t,
                                  const void*, int64_t, double, void*, int64_t, cudaStream_t);
@@ -1103,10 +1143,24 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
   V* rowj = cand_data + 2 * G_cap * nb;
   unsigned arrivals = 0;  // grid-barrier arrivals so far (the counter starts at zero)
   fosb_status st = FOSB_OK;
-  // one 64-column panel at column j0: cooperative factorisation + row swaps elsewhere
+  // complex64: tournament-pivoting panels (no grid-wide waits); complex128: cooperative
+  // partial pivoting with one grid barrier per column
+  char* tslu_scr = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tslu_scr), tslu_scratch_bytes(n), s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(scratch, s);
+      return cuda_fail(e, "getrf: panel scratch");
+    }
+  }
+  // one 64-column panel at column j0, then its row interchanges on every other column
   auto panel_step = [&](int64_t j0, int jb) -> cudaError_t {
-    cudaError_t e = launch_panel<T>(A + j0 * lda + j0, n - j0, jb, lda, ipiv + j0, j0, scr, arrivals,
-                                    cand_data, rowj, d_status, int64_t(G_cap), nsm, s);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4)
+      e = tslu_panel(A + j0 * lda + j0, n - j0, jb, lda, ipiv + j0, j0, tslu_scr, n, d_status, s);
+    else
+      e = launch_panel<T>(A + j0 * lda + j0, n - j0, jb, lda, ipiv + j0, j0, scr, arrivals, cand_data, rowj,
+                          d_status, int64_t(G_cap), nsm, s);
     if (e != cudaSuccess) return e;
     laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
     note_launches(2);  // panel + row swaps
@@ -1172,6 +1226,7 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
     }
   }
   cudaFreeAsync(scratch, s);
+  if (tslu_scr) cudaFreeAsync(tslu_scr, s);
   return st;
 }
 
