@@ -4,19 +4,13 @@
 // Re(C) -= Ar Br - Ai Bi and Im(C) -= Ar Bi + Ai Br give 12 MMAs (M = 128, N = 128,
 // K = 8) per k-slab of 8; the minus sign of Ai Bi uses the instruction's negate-A bit.
 //
-// CTA = 256 threads, output tile 128 x 128 complex; accumulators Re and Im in TMEM
-// (128 lanes x 128 fp32 columns each, 256 columns allocated).  K is consumed in chunks of
-// 16: the threads load the chunk from global memory (row-major complex64), split it and
-// store it in the canonical no-swizzle K-major layout (8 x 16-byte core matrices; LBO =
-// 128 B between the two core matrices of a k-slab, SBO = 256 B between 8-row groups); one
-// thread issues the MMAs and commits them to an mbarrier; the next chunk overwrites shared
-// memory only after that mbarrier completes.  The epilogue moves the accumulators
-// TMEM -> registers -> shared memory (padded rows) and updates C with coalesced 16-byte
-// read-modify-writes, 64 columns at a time.  Two CTAs per SM (68 KB shared memory each)
-// let one CTA's MMAs overlap the other's staging and epilogue.  Every wait is bounded:
-// on time-out the status word is set to FOSB_ERR_TIMEOUT, outstanding MMAs get a second
-// bounded wait, TMEM is freed and the CTA returns.
+// Output tile 128 x 128 complex; accumulators Re and Im in TMEM (128 lanes x 128 fp32
+// columns each).  K is consumed in chunks of 16, stored split in the canonical no-swizzle
+// K-major layout (8 x 16-byte core matrices; LBO = 128 B between the two core matrices of a
+// k-slab, SBO = 256 B between 8-row groups).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include <cstdint>
 
@@ -30,12 +24,7 @@ constexpr int SLAB = 128 * 8 * 4;                        // bytes per k-slab of 
 constexpr int PART = SLAB * (TC_KC / 8);                 // 8192 bytes per part per chunk
 constexpr int SMEM_A = 4 * PART, SMEM_B = 4 * PART;      // parts: re_b, re_s, im_b, im_s
 constexpr int EPI_LD = 65;                               // padded float2 row stride of the epilogue tile
-constexpr int SMEM_EPI = TC_M * EPI_LD * 8;              // 66560 bytes (aliases the operand buffers)
-constexpr int SMEM_BODY = (SMEM_A + SMEM_B) > SMEM_EPI ? (SMEM_A + SMEM_B) : SMEM_EPI;
-// 100 KB requested (66.5 KB used + alignment slack) so that at most two CTAs share an SM:
-// 2 x 256 TMEM columns fill its 512 exactly and tcgen05.alloc never has to wait.
-constexpr int TC_SMEM = 100 * 1024;
-static_assert(SMEM_BODY + 1024 <= TC_SMEM, "tile does not fit the shared-memory request");
+constexpr int SMEM_EPI = TC_M * EPI_LD * 8;              // 66560 bytes (epilogue transpose tile)
 constexpr int TMEM_COLS = 256;
 constexpr long long kMmaSpinLimit = 1ll << 24;
 
@@ -100,179 +89,279 @@ __device__ __forceinline__ void store_split(unsigned char* base, int off, float2
   *reinterpret_cast<float*>(base + 3 * PART + off) = tf32_round(v.y - ib);
 }
 
-__global__ void __launch_bounds__(256, 2) cgemm_update_tc_kernel(int64_t M, int64_t N, int64_t K, const float2* __restrict__ A,
-                                                              int64_t lda, const float2* __restrict__ B, int64_t ldb,
-                                                              float2* __restrict__ C, int64_t ldc, int* status,
-                                                              int vec_ok) {
+// ---------------------------------------------------------------------------------------
+// Persistent, warp-specialised form of the same update (one CTA per SM, tiles strided over
+// the grid).  Roles:
+//   warps 0-7  producers: global -> registers -> 3xTF32 split -> stage s of a 2-stage
+//              shared-memory ring (64 KB per stage), then arrive on full[s];
+//   warp 8     MMA issuer: per chunk waits full[s], issues the 24 MMAs into accumulator
+//              buffer b (two buffers x 256 TMEM columns), commits to empty[s]; after a
+//              tile's last chunk commits to tmem_full[b];
+//   warps 9-12 epilogue (TMEM lane groups 1, 2, 3, 0): wait tmem_full[b], drain the
+//              accumulators, release the buffer on tmem_empty[b], then update C through a
+//              padded shared tile with coalesced 16-byte read-modify-writes.
+// So the C traffic of tile i overlaps the MMAs of tile i + 1, and staging overlaps MMAs.
+// Every wait is bounded; a time-out sets the status word, raises an abort flag that all
+// roles poll, and the MMA thread drains its outstanding MMAs before TMEM is freed.
+constexpr int WS_STAGES = 2;
+constexpr int WS_STAGE_BYTES = SMEM_A + SMEM_B;                       // 64 KB
+constexpr int WS_EPI_OFF = WS_STAGES * WS_STAGE_BYTES;                // 128 KB
+constexpr int WS_SMEM = WS_EPI_OFF + SMEM_EPI + 1024;                 // + alignment slack
+constexpr int WS_THREADS = 13 * 32;
+constexpr int WS_PRODUCERS = 256;
+static_assert(WS_SMEM <= 227 * 1024, "warp-specialised tile does not fit shared memory");
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(a));
+}
+__device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n)); }
+
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    cgemm_update_tc_ws_kernel(int64_t M, int64_t N, int64_t K, const float2* __restrict__ A, int64_t lda,
+                              const float2* __restrict__ B, int64_t ldb, float2* __restrict__ C, int64_t ldc,
+                              int* status, int vec_ok) {
   extern __shared__ unsigned char tc_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sA = smem;           // 4 parts x 2 slabs x 4096
-  unsigned char* sB = smem + SMEM_A;  // 4 parts x 2 slabs x 4096
-  float2* sE = reinterpret_cast<float2*>(smem);  // epilogue tile (after the last MMA)
-  __shared__ uint64_t mbar;
+  float2* sE = reinterpret_cast<float2*>(smem + WS_EPI_OFF);
+  __shared__ uint64_t bar_full[WS_STAGES], bar_empty[WS_STAGES], bar_tfull[2], bar_tempty[2], bar_drain;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int abort_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ volatile int epi_stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t row0 = int64_t(blockIdx.y) * TC_M, col0 = int64_t(blockIdx.x) * TC_N;
-  const uint32_t mbar_addr = smem_u32(&mbar);
+  const int64_t tiles_n = (N + TC_N - 1) / TC_N, tiles = tiles_n * ((M + TC_M - 1) / TC_M);
+  const int64_t nchunk = (K + TC_KC - 1) / TC_KC;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(TMEM_COLS));
+                 "r"(2 * TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_addr));
+    for (int i = 0; i < WS_STAGES; ++i) {
+      mbar_init(smem_u32(&bar_full[i]), WS_PRODUCERS);
+      mbar_init(smem_u32(&bar_empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bar_tfull[i]), 1);
+      mbar_init(smem_u32(&bar_tempty[i]), 128);
+    }
+    mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_sh = 0;
+    epi_stop = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_sh;
-  const uint32_t d_re = tmem, d_im = tmem + TC_N;
-  uint32_t phase = 0;
-  const int64_t nchunk = (K + TC_KC - 1) / TC_KC;
-  // Staging maps (per 32-lane group: k3 = lane & 3, rc = lane >> 2): every warp load covers
-  // 8 rows x 4 consecutive k (A) or 4 k-rows x 8 consecutive columns (B) -- whole 32-byte
-  // sectors -- and the K-major store offsets (rc * 16 + k3 * 4 within a core matrix) hit 32
-  // distinct banks.
-  const int k3 = lane & 3, rc = lane >> 2;
-  float2 va[8], vb[8];
-  auto load_chunk = [&](int64_t k0) {
-#pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      const int w = warp + 8 * it;                       // 0..63
-      const int khi = w & 3, rg = w >> 2;                // A: k-quad, 8-row group
-      const int r = rg * 8 + rc, kk = (khi >> 1) * 8 + (khi & 1) * 4 + k3;
-      const int64_t gr = row0 + r, gk = k0 + kk;
-      va[it] = (gr < M && gk < K) ? A[gr * lda + gk] : make_float2(0.f, 0.f);
-      const int cg = w & 15, kb = w >> 4;                // B: 8-column group, k-quad
-      const int c = cg * 8 + rc, kkb = (kb >> 1) * 8 + (kb & 1) * 4 + k3;
-      const int64_t gc = col0 + c, gkb = k0 + kkb;
-      vb[it] = (gc < N && gkb < K) ? B[gkb * ldb + gc] : make_float2(0.f, 0.f);
-    }
+  auto fail = [&]() {
+    abort_sh = 1;
+    atomicExch(status, FOSB_ERR_TIMEOUT);
   };
-  if (nchunk > 0) load_chunk(0);
-  for (int64_t ch = 0; ch < nchunk; ++ch) {
-    // ---- split and store the chunk held in registers (K-major, canonical layout)
+
+  if (warp < 8) {
+    // ------------------------------------------------------------ producers
+    const int k3 = lane & 3, rc = lane >> 2;
+    float2 va[8], vb[8];
+    auto load_chunk = [&](int64_t row0, int64_t col0, int64_t k0) {
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      const int w = warp + 8 * it;
-      const int khi = w & 3, rg = w >> 2;
-      const int r = rg * 8 + rc, k8 = (khi & 1) * 4 + k3;
-      store_split(sA, (khi >> 1) * SLAB + kmajor_off(r, k8), va[it]);
-      const int cg = w & 15, kb = w >> 4;
-      const int c = cg * 8 + rc, k8b = (kb & 1) * 4 + k3;
-      store_split(sB, (kb >> 1) * SLAB + kmajor_off(c, k8b), vb[it]);
+      for (int it = 0; it < 8; ++it) {
+        const int w = warp + 8 * it;
+        const int khi = w & 3, rg = w >> 2;
+        const int r = rg * 8 + rc, kk = (khi >> 1) * 8 + (khi & 1) * 4 + k3;
+        const int64_t gr = row0 + r, gk = k0 + kk;
+        va[it] = (gr < M && gk < K) ? A[gr * lda + gk] : make_float2(0.f, 0.f);
+        const int cg = w & 15, kb = w >> 4;
+        const int c = cg * 8 + rc, kkb = (kb >> 1) * 8 + (kb & 1) * 4 + k3;
+        const int64_t gc = col0 + c, gkb = k0 + kkb;
+        vb[it] = (gc < N && gkb < K) ? B[gkb * ldb + gc] : make_float2(0.f, 0.f);
+      }
+    };
+    int64_t it_glob = 0;
+    bool have = false;
+    int64_t tile = blockIdx.x;
+    if (tile < tiles) {
+      load_chunk((tile / tiles_n) * TC_M, (tile % tiles_n) * TC_N, 0);
+      have = true;
     }
-    asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor core
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    for (; tile < tiles && have; tile += gridDim.x) {
+      const int64_t row0 = (tile / tiles_n) * TC_M, col0 = (tile % tiles_n) * TC_N;
+      for (int64_t ch = 0; ch < nchunk; ++ch, ++it_glob) {
+        const int st = int(it_glob % WS_STAGES);
+        const int64_t use = it_glob / WS_STAGES;
+        if (use > 0 && !mbar_wait(smem_u32(&bar_empty[st]), uint32_t((use - 1) & 1))) fail();
+        if (abort_sh) {
+          have = false;
+          break;
+        }
+        unsigned char* sA = smem + st * WS_STAGE_BYTES;
+        unsigned char* sB = sA + SMEM_A;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int w = warp + 8 * it;
+          const int khi = w & 3, rg = w >> 2;
+          const int r = rg * 8 + rc, k8 = (khi & 1) * 4 + k3;
+          store_split(sA, (khi >> 1) * SLAB + kmajor_off(r, k8), va[it]);
+          const int cg = w & 15, kb = w >> 4;
+          const int c = cg * 8 + rc, k8b = (kb & 1) * 4 + k3;
+          store_split(sB, (kb >> 1) * SLAB + kmajor_off(c, k8b), vb[it]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        mbar_arrive(smem_u32(&bar_full[st]));
+        // prefetch the next chunk (this tile's or the next tile's first) while MMAs run
+        if (ch + 1 < nchunk) {
+          load_chunk(row0, col0, (ch + 1) * TC_KC);
+        } else if (tile + gridDim.x < tiles) {
+          const int64_t nt = tile + gridDim.x;
+          load_chunk((nt / tiles_n) * TC_M, (nt % tiles_n) * TC_N, 0);
+        }
+      }
+    }
+  } else if (warp == 8) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
       const uint32_t id = idesc_tf32(TC_M, TC_N, false), idn = idesc_tf32(TC_M, TC_N, true);
+      int64_t it_glob = 0, tcount = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !abort_sh; tile += gridDim.x, ++tcount) {
+        const int b = int(tcount & 1);
+        const int64_t ub = tcount >> 1;
+        if (ub > 0 && !mbar_wait(smem_u32(&bar_tempty[b]), uint32_t((ub - 1) & 1))) {
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t d_re = tmem + uint32_t(b) * TMEM_COLS, d_im = d_re + TC_N;
+        for (int64_t ch = 0; ch < nchunk; ++ch, ++it_glob) {
+          const int st = int(it_glob % WS_STAGES);
+          const int64_t use = it_glob / WS_STAGES;
+          if (!mbar_wait(smem_u32(&bar_full[st]), uint32_t(use & 1))) {
+            fail();
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = smem_u32(smem + st * WS_STAGE_BYTES), b0 = a0 + SMEM_A;
 #pragma unroll
-      for (int s = 0; s < TC_KC / 8; ++s) {
-        const uint64_t arb = smem_desc(a0 + 0 * PART + s * SLAB), ars = smem_desc(a0 + 1 * PART + s * SLAB);
-        const uint64_t aib = smem_desc(a0 + 2 * PART + s * SLAB), ais = smem_desc(a0 + 3 * PART + s * SLAB);
-        const uint64_t brb = smem_desc(b0 + 0 * PART + s * SLAB), brs = smem_desc(b0 + 1 * PART + s * SLAB);
-        const uint64_t bib = smem_desc(b0 + 2 * PART + s * SLAB), bis = smem_desc(b0 + 3 * PART + s * SLAB);
-        const uint32_t acc0 = (ch > 0 || s > 0) ? 1u : 0u;
-        // Re += Ar Br - Ai Bi
-        mma_tf32(d_re, arb, brb, id, acc0);
-        mma_tf32(d_re, arb, brs, id, 1u);
-        mma_tf32(d_re, ars, brb, id, 1u);
-        mma_tf32(d_re, aib, bib, idn, 1u);
-        mma_tf32(d_re, aib, bis, idn, 1u);
-        mma_tf32(d_re, ais, bib, idn, 1u);
-        // Im += Ar Bi + Ai Br
-        mma_tf32(d_im, arb, bib, id, acc0);
-        mma_tf32(d_im, arb, bis, id, 1u);
-        mma_tf32(d_im, ars, bib, id, 1u);
-        mma_tf32(d_im, aib, brb, id, 1u);
-        mma_tf32(d_im, aib, brs, id, 1u);
-        mma_tf32(d_im, ais, brb, id, 1u);
+          for (int sl = 0; sl < TC_KC / 8; ++sl) {
+            const uint64_t arb = smem_desc(a0 + 0 * PART + sl * SLAB), ars = smem_desc(a0 + 1 * PART + sl * SLAB);
+            const uint64_t aib = smem_desc(a0 + 2 * PART + sl * SLAB), ais = smem_desc(a0 + 3 * PART + sl * SLAB);
+            const uint64_t brb = smem_desc(b0 + 0 * PART + sl * SLAB), brs = smem_desc(b0 + 1 * PART + sl * SLAB);
+            const uint64_t bib = smem_desc(b0 + 2 * PART + sl * SLAB), bis = smem_desc(b0 + 3 * PART + sl * SLAB);
+            const uint32_t acc0 = (ch > 0 || sl > 0) ? 1u : 0u;
+            mma_tf32(d_re, arb, brb, id, acc0);
+            mma_tf32(d_re, arb, brs, id, 1u);
+            mma_tf32(d_re, ars, brb, id, 1u);
+            mma_tf32(d_re, aib, bib, idn, 1u);
+            mma_tf32(d_re, aib, bis, idn, 1u);
+            mma_tf32(d_re, ais, bib, idn, 1u);
+            mma_tf32(d_im, arb, bib, id, acc0);
+            mma_tf32(d_im, arb, bis, id, 1u);
+            mma_tf32(d_im, ars, bib, id, 1u);
+            mma_tf32(d_im, aib, brb, id, 1u);
+            mma_tf32(d_im, aib, brs, id, 1u);
+            mma_tf32(d_im, ais, brb, id, 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&bar_empty[st])));
+        }
+        if (abort_sh) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar_tfull[b])));
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr));
+      // drain: completes once every MMA issued above has finished
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&bar_drain)));
+      if (!mbar_wait(smem_u32(&bar_drain), 0u)) fail();
     }
-    // the next chunk's global loads are in flight while the MMAs run
-    if (ch + 1 < nchunk) load_chunk((ch + 1) * TC_KC);
-    // all threads wait for the MMAs (shared memory is reused by the next chunk)
-    if (!mbar_wait(mbar_addr, phase)) abort_sh = 1;
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-    if (abort_sh) break;
-  }
-  if (abort_sh) {
-    if (tid == 0) {
-      atomicExch(status, FOSB_ERR_TIMEOUT);
-      mbar_wait(mbar_addr, phase);  // second bounded wait for MMAs still in flight
-    }
-    __syncthreads();
-  } else if (nchunk > 0) {
-    // ---- epilogue in two halves of 64 columns: TMEM -> registers -> shared -> C
-    const int lane_base = (warp & 3) * 32, csub = (warp >> 2) * 32;
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (128 threads)
+    const int et = tid - 9 * 32;              // 0..127
+    const int lane_base = (warp & 3) * 32;    // TMEM lane group of this warp
     const int r_local = lane_base + lane;
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      uint32_t vr[32], vi[32];
-      tmem_ld32(d_re + (uint32_t(lane_base) << 16) + h * 64 + csub, vr);
-      tmem_ld32(d_im + (uint32_t(lane_base) << 16) + h * 64 + csub, vi);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int j = 0; j < 32; ++j) sE[r_local * EPI_LD + csub + j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
-      __syncthreads();
-      // coalesced update: a warp covers one row's 64 complex (512 B) per pass; all loads
-      // are issued before any store
-      if (vec_ok) {
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-        float4 o[8];
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int e = tid + 256 * (it + 8 * pass);  // 0 .. 4095 pairs of complex
-          const int r = e >> 5, c = (e & 31) * 2;
-          const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
-          o[it] = (gr < M && gc + 1 < N) ? *reinterpret_cast<const float4*>(C + gr * ldc + gc) : make_float4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int e = tid + 256 * (it + 8 * pass);
-          const int r = e >> 5, c = (e & 31) * 2;
-          const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
-          if (gr < M && gc + 1 < N) {
-            const float2 d0 = sE[r * EPI_LD + c], d1 = sE[r * EPI_LD + c + 1];
-            *reinterpret_cast<float4*>(C + gr * ldc + gc) =
-                make_float4(o[it].x - d0.x, o[it].y - d0.y, o[it].z - d1.x, o[it].w - d1.y);
-          } else if (gr < M && gc < N) {  // ragged last column
-            float2 v = C[gr * ldc + gc];
-            const float2 d0 = sE[r * EPI_LD + c];
-            C[gr * ldc + gc] = make_float2(v.x - d0.x, v.y - d0.y);
-          }
-        }
-        }
-      } else {
-#pragma unroll 8
-        for (int it = 0; it < 32; ++it) {
-          const int e = tid + 256 * it;  // 0 .. 8191
-          const int r = e >> 6, c = e & 63;
-          const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
-          if (gr < M && gc < N) {
-            const float2 d = sE[r * EPI_LD + c];
-            float2 o = C[gr * ldc + gc];
-            o.x -= d.x;
-            o.y -= d.y;
-            C[gr * ldc + gc] = o;
-          }
-        }
+    int64_t tcount = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tcount) {
+      const int b = int(tcount & 1);
+      const int64_t ub = tcount >> 1;
+      // the stop decision must be the same in all four epilogue warps (they share named
+      // barriers): a flag written before and read after one
+      if (!mbar_wait(smem_u32(&bar_tfull[b]), uint32_t(ub & 1))) {
+        fail();
+        epi_stop = 1;
       }
-      __syncthreads();
+      named_bar(1, 128);
+      if (epi_stop) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t d_re = tmem + uint32_t(b) * TMEM_COLS, d_im = d_re + TC_N;
+      const int64_t row0 = (tile / tiles_n) * TC_M, col0 = (tile % tiles_n) * TC_N;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+        for (int cs = 0; cs < 2; ++cs) {
+          uint32_t vr[32], vi[32];
+          tmem_ld32(d_re + (uint32_t(lane_base) << 16) + h * 64 + cs * 32, vr);
+          tmem_ld32(d_im + (uint32_t(lane_base) << 16) + h * 64 + cs * 32, vi);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            sE[r_local * EPI_LD + cs * 32 + j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+        }
+        if (h == 1) {  // every accumulator value of this buffer is in registers / shared memory now
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(smem_u32(&bar_tempty[b]));
+        }
+        named_bar(1, 128);
+        if (vec_ok) {
+#pragma unroll 1
+          for (int pass = 0; pass < 4; ++pass) {
+            float4 o[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int e = et + 128 * (q + 8 * pass);  // 0 .. 4095 pairs of complex
+              const int r = e >> 5, c = (e & 31) * 2;
+              const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+              o[q] = (gr < M && gc + 1 < N) ? *reinterpret_cast<const float4*>(C + gr * ldc + gc)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int e = et + 128 * (q + 8 * pass);
+              const int r = e >> 5, c = (e & 31) * 2;
+              const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+              if (gr < M && gc + 1 < N) {
+                const float2 d0 = sE[r * EPI_LD + c], d1 = sE[r * EPI_LD + c + 1];
+                *reinterpret_cast<float4*>(C + gr * ldc + gc) =
+                    make_float4(o[q].x - d0.x, o[q].y - d0.y, o[q].z - d1.x, o[q].w - d1.y);
+              } else if (gr < M && gc < N) {
+                float2 v = C[gr * ldc + gc];
+                const float2 d0 = sE[r * EPI_LD + c];
+                C[gr * ldc + gc] = make_float2(v.x - d0.x, v.y - d0.y);
+              }
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int q = 0; q < 64; ++q) {
+            const int e = et + 128 * q;  // 0 .. 8191
+            const int r = e >> 6, c = e & 63;
+            const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+            if (gr < M && gc < N) {
+              const float2 d = sE[r * EPI_LD + c];
+              float2 o = C[gr * ldc + gc];
+              o.x -= d.x;
+              o.y -= d.y;
+              C[gr * ldc + gc] = o;
+            }
+          }
+        }
+        named_bar(1, 128);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
 }
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
@@ -284,21 +373,25 @@ cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int6
                             void* C, int64_t ldc, int* status, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   static bool attr[64] = {};
+  static int nsm[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(cgemm_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(cgemm_update_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  dim3 grid(cdiv(N, TC_N), cdiv(M, TC_M));
-  if (grid.y > 65535u) return cudaErrorInvalidValue;
+  const int64_t tiles = int64_t(cdiv(N, TC_N)) * cdiv(M, TC_M);
+  const unsigned grid = unsigned(std::min<int64_t>(tiles, std::max(nsm[dev], 1)));  // persistent: one CTA per SM
   // 16-byte epilogue accesses need a 16-byte aligned C with an even leading dimension
   const int vec_ok = (reinterpret_cast<uintptr_t>(C) % 16 == 0) && (ldc % 2 == 0);
   ProfScope prof("lu_update", s, 8.0 * double(M) * double(N) * double(K));
-  cgemm_update_tc_kernel<<<grid, 256, TC_SMEM, s>>>(M, N, K, static_cast<const float2*>(A), lda,
-                                                   static_cast<const float2*>(B), ldb, static_cast<float2*>(C), ldc,
-                                                   status, vec_ok);
+  cgemm_update_tc_ws_kernel<<<grid, WS_THREADS, WS_SMEM, s>>>(M, N, K, static_cast<const float2*>(A), lda,
+                                                             static_cast<const float2*>(B), ldb,
+                                                             static_cast<float2*>(C), ldc, status, vec_ok);
   return launched();
 }
 
