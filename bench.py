@@ -187,7 +187,8 @@ def run_fosb(args):
     tf32_peak = bf16 * TF32_PER_BF16  # measured bf16 burst x nominal TF32/bf16 ratio
     # algorithmic work -> (bound, flops, peak, kernel, note) per family
     fam_model = {
-        "lu_update": ("tensor", 1.0, tf32_peak, "cgemm_update_tc_kernel (tcgen05 kind::tf32, 3xTF32 complex)",
+        "lu_update": ("tensor", 1.0, tf32_peak,
+                      "cgemm_update_tc_ws_kernel (persistent warp-specialised tcgen05 kind::tf32, 3xTF32 complex)",
                       f"TF32 dense = measured bf16 {bf16} x 1.1/2.25; work = useful complex flops 8MNK "
                       "(3xTF32 executes 3x that on the tensor pipe, so frac <= 1/3)"),
         "asm_regular": ("alu", 27.0, FP32_PEAK_TFLOPS if arith == F.ASM_FF else FP64_PEAK_TFLOPS,
