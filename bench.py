@@ -31,10 +31,17 @@ METRIC = "FOSB covariance time & EFIE entries/s, mixed vs FP64 on one GB300 at 1
 
 WORKLOADS = {
     # mixed-precision sphere, levels l = 0..4 are icospheres of T = 80 * 4**l triangles
-    "sphere-ka4-ct-L4": dict(levels=[0, 1, 2, 3, 4], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=4),
+    "sphere-ka4-ct-L4": dict(mesh="sphere", levels=[0, 1, 2, 3, 4], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=4,
+                             d=(0, 0, 1), p=(1, 0, 0), dirs="hplane", kernel="gauss"),
     # smaller cases of the same kernels (profiling captures)
-    "sphere-ka4-ct-L3": dict(levels=[0, 1, 2, 3], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=3),
-    "sphere-ka4-ct-L2": dict(levels=[0, 1, 2], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=2),
+    "sphere-ka4-ct-L3": dict(mesh="sphere", levels=[0, 1, 2, 3], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=3,
+                             d=(0, 0, 1), p=(1, 0, 0), dirs="hplane", kernel="gauss"),
+    "sphere-ka4-ct-L2": dict(mesh="sphere", levels=[0, 1, 2], k=4.0, sigma=0.005, ell=0.3, n_dir=181, L0=0, L=2,
+                             d=(0, 0, 1), p=(1, 0, 0), dirs="hplane", kernel="gauss"),
+    # largest: torus R = 1, r = 0.35, levels 1..5 = grids 10x4 .. 160x64 (T = 80 .. 20480), k a = 10,
+    # Matern-3/2 (std 0.002, l = 0.2), 361 directions in the z = 0 plane, d = x, p = z
+    "torus-ka10-ct-L5": dict(mesh="torus", levels=[1, 2, 3, 4, 5], k=10.0, sigma=0.002, ell=0.2, n_dir=361, L0=1,
+                             L=5, d=(1, 0, 0), p=(0, 0, 1), dirs="zplane", kernel="matern32"),
 }
 
 # Derived ALU peaks (from the SM count and clock): FP32 152 SMs x 128 lanes x 2 x 2.07 GHz;
@@ -54,10 +61,30 @@ def _peaks():
         return {}
 
 
-def _meshes(levels):
+def _meshes(W):
     import fosb_synth as S
 
-    return [S.icosphere(l + 1) for l in levels]
+    if W["mesh"] == "torus":
+        return S.torus_hierarchy(W["levels"])
+    return [S.icosphere(l + 1) for l in W["levels"]]
+
+
+def _dirs(W):
+    import fosb_synth as S
+
+    return S.zplane_directions(W["n_dir"]) if W["dirs"] == "zplane" else S.hplane_directions(W["n_dir"])
+
+
+def _n_edges(W, l):
+    return 120 * 4 ** (l - 1) if W["mesh"] == "torus" else 120 * 4**l
+
+
+def _problem(F, W, meshes, dirs, prec, arith):
+    from paper_2308_01457_gb300.ct import FOSBProblem
+
+    kern = F.COV_MATERN32 if W["kernel"] == "matern32" else F.COV_GAUSS
+    return FOSBProblem(meshes, W["k"], W["d"], W["p"], dirs, W["L0"], W["L"], kern, W["sigma"], W["ell"], prec=prec,
+                       arith=arith).setup()
 
 
 def _clock_sampler(gpu_index: int):
@@ -113,8 +140,6 @@ def run_fosb(args):
     import torch
 
     import paper_2308_01457_gb300 as F
-    from paper_2308_01457_gb300.ct import FOSBProblem
-    import fosb_synth as S
 
     F.build.build()
     ws, rank, local = _dist()
@@ -124,11 +149,10 @@ def run_fosb(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     W = WORKLOADS[args.workload]
-    meshes = _meshes(W["levels"])
-    dirs = S.hplane_directions(W["n_dir"])
+    meshes = _meshes(W)
+    dirs = _dirs(W)
     arith = F.ASM_FF if args.arith == "ff" else F.ASM_FP64
-    prob = FOSBProblem(meshes, W["k"], (0, 0, 1), (1, 0, 0), dirs, W["L0"], W["L"], F.COV_GAUSS, W["sigma"], W["ell"],
-                       prec=F.MIXED, arith=arith).setup()
+    prob = _problem(F, W, meshes, dirs, F.MIXED, arith)
     L = W["L"]
     N = {l: prob.levels[l].mesh.n_edges for l in prob.levels}
 
@@ -264,10 +288,8 @@ def run_fp64_compare(W, meshes, dirs, out_mixed, ms_mixed):
     import torch
 
     import paper_2308_01457_gb300 as F
-    from paper_2308_01457_gb300.ct import FOSBProblem
 
-    prob = FOSBProblem(meshes, W["k"], (0, 0, 1), (1, 0, 0), dirs, W["L0"], W["L"], F.COV_GAUSS, W["sigma"],
-                       W["ell"], prec=F.FP64, arith=F.ASM_FP64).setup()
+    prob = _problem(F, W, meshes, dirs, F.FP64, F.ASM_FP64)
     timers = {}
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -302,7 +324,6 @@ def run_e2e(args, W, meshes, dirs, arith):
     import torch
 
     import paper_2308_01457_gb300 as F
-    from paper_2308_01457_gb300.ct import FOSBProblem
 
     pinned = []
     h2d = 0
@@ -321,8 +342,7 @@ def run_e2e(args, W, meshes, dirs, arith):
     for i in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        prob = FOSBProblem(pinned, W["k"], (0, 0, 1), (1, 0, 0), dirs, W["L0"], W["L"], F.COV_GAUSS, W["sigma"],
-                           W["ell"], prec=F.MIXED, arith=arith).setup()
+        prob = _problem(F, W, pinned, dirs, F.MIXED, arith)
         Fm, cov = prob.run()
         F_h.copy_(Fm, non_blocking=True)
         C_h.copy_(cov, non_blocking=True)
@@ -350,7 +370,7 @@ def cpu_baseline(W, budget_s: float = 20.0):
     # assembly sample: the largest level that fits the budget (start small)
     asm_rate, asm_lvl = None, None
     for lvl in (2, 3):
-        m = O.from_synth(S.icosphere(lvl))
+        m = O.from_synth(S.icosphere(lvl) if W["mesh"] == "sphere" else S.torus(10 * 2 ** (lvl - 1), 4 * 2 ** (lvl - 1)))
         t0 = time.perf_counter()
         O.assemble_z(m, W["k"])
         dt = time.perf_counter() - t0
@@ -372,7 +392,7 @@ def cpu_baseline(W, budget_s: float = 20.0):
         t0 = time.perf_counter()
         np.linalg.solve(A, b)
         lu_rate = (8.0 / 3.0) * n_lu**3 / (time.perf_counter() - t0)
-    N = {l: 120 * 4**l for l in W["levels"]}
+    N = {l: _n_edges(W, l) for l in W["levels"]}
     t_asm = sum(N[l] ** 2 / asm_rate for l in N)
     t_lu = lambda n: (8.0 / 3.0) * n**3 / lu_rate  # noqa: E731
     t_nominal = sum(t_lu(N[l]) for l in N)
@@ -383,7 +403,7 @@ def cpu_baseline(W, budget_s: float = 20.0):
         t_cov += t_lu(N[a]) + t_lu(N[c]) + 8.0 * (N[a] ** 2 * N[c] + N[c] ** 2 * N[a]) / lu_rate
     total = t_asm + t_nominal + t_cov
     return {"value": round(total, 2), "unit": "s per FOSB step", "cores": cores, "kind": "oracle",
-            "sample": f"oracle assembly of icosphere level {asm_lvl} ({asm_rate:.3e} entries/s) and LAPACK complex LU "
+            "sample": f"oracle assembly of the level-{asm_lvl} mesh ({asm_rate:.3e} entries/s) and LAPACK complex LU "
                       f"at N={n_lu} ({lu_rate / 1e9:.1f} GFLOP/s), extrapolated to the full step "
                       f"(N^2 assembly, N^3 factorisations); sample time {time.perf_counter() - t_begin:.1f} s",
             "assembly_entries_per_s": round(asm_rate, 1)}

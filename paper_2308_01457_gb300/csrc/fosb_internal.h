@@ -185,6 +185,12 @@ fosb_status getrf_external_scratch(void* A, int64_t n, int64_t lda, int32_t* ipi
 template <typename T>
 cudaError_t getrs(const void* LU, int64_t n, int64_t ldlu, const int32_t* ipiv, void* X, int64_t nrhs, int64_t ldx,
                   cudaStream_t s, int* status = nullptr);
+// One whole triangular sweep with complex64 factors (unit lower if upper == 0, else upper
+// with its diagonal) for nrhs <= 8 right-hand sides stored dense (n x nrhs); scratch holds
+// trsv_stream_scratch_ints(n) ints; a bounded wait that gives up sets *status.
+size_t trsv_stream_scratch_ints(int64_t n);
+cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, void* X, int64_t nrhs, int upper, int* scratch,
+                            int* status, cudaStream_t s);
 cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                 cudaStream_t s);
 cudaError_t convert_c64_to_c128(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,

@@ -1298,6 +1298,19 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(V) * n * nrhs, s);
   if (e != cudaSuccess) return e;
   gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
+  if (sizeof(T) == 4 && status && nrhs <= 8) {
+    // few right-hand sides: one persistent streaming kernel per sweep
+    int* flags = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&flags), sizeof(int) * trsv_stream_scratch_ints(n), s);
+    if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, tmp, nrhs, 0, flags, status, s);
+    if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, tmp, nrhs, 1, flags, status, s);
+    if (flags) cudaFreeAsync(flags, s);
+    if (e != cudaSuccess) return e;
+    copy_kernel<V><<<cdiv(n * nrhs, 256), 256, 0, s>>>(tmp, n, nrhs, nrhs, X, ldx);
+    note_launches(2);  // gather + final copy
+    cudaFreeAsync(tmp, s);
+    return cudaGetLastError();
+  }
   const int nb = 64;
   enable_trsv_smem<T>();
   auto diag = [&](int64_t i0, int ib, int upper) {
