@@ -77,7 +77,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   }
   if (lu->prec == FOSB_FP32) {
     if (X != B) FOSB_CUDA(copy_matrix(B, n, nrhs, ldb, X, ldx, 8, s));
-    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, X, nrhs, ldx, s, lu->d_status));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, X, nrhs, ldx, s, lu->d_status, lu->dinv));
     return FOSB_OK;
   }
   // MIXED: complex64 factors, FP64 residuals.
@@ -101,7 +101,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   FOSB_TRY(col_norms(Bsrc, n, nrhs, ldbs, nb.as<double>(), bn, s));
   // x0
   FOSB_CUDA(convert_c128_to_c64(Bsrc, n, nrhs, ldbs, d.p, nrhs, s));
-  FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status));
+  FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status, lu->dinv));
   FOSB_CUDA(convert_c64_to_c128(d.p, n, nrhs, nrhs, X, ldx, s));
   double prev = INFINITY, prev2 = INFINITY, berr = INFINITY;
   int it = 0;
@@ -122,7 +122,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
     prev2 = prev;
     prev = berr;
     FOSB_CUDA(convert_c128_to_c64(r.p, n, nrhs, nrhs, d.p, nrhs, s));
-    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status, lu->dinv));
     FOSB_CUDA(axpy_c64_into_c128(d.p, n, nrhs, nrhs, X, ldx, s));
     ++it;
   }
@@ -246,6 +246,11 @@ fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu
   }
   if ((e = cudaMemcpy(lu->ipiv, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice)))
     return cleanup(cuda_fail(e, "fosb_factor: permutation"));
+  if (prec != FOSB_FP64) {  // inverted diagonal blocks for the streaming triangular sweeps
+    if ((e = cudaMalloc(&lu->dinv, tri_block_inverses_bytes(n))) != cudaSuccess ||
+        (e = tri_block_inverses_c64(lu->lu, n, n, lu->dinv, s)) != cudaSuccess)
+      return cleanup(cuda_fail(e, "fosb_factor: diagonal-block inverses"));
+  }
   *out = lu;
   return FOSB_OK;
 }
@@ -272,6 +277,7 @@ fosb_status fosb_lu_destroy(fosb_lu lu) {
   if (lu->ipiv) cudaFree(lu->ipiv);
   if (lu->d_status) cudaFree(lu->d_status);
   if (lu->zff) cudaFree(lu->zff);
+  if (lu->dinv) cudaFree(lu->dinv);
   delete lu;
   return FOSB_OK;
 }

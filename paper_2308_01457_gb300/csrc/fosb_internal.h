@@ -106,6 +106,7 @@ struct fosb_lu_s {
   const void* zref = nullptr;  // MIXED: non-owning complex128 Z for residuals
   int64_t ldz = 0;
   void* zff = nullptr;         // MIXED: (hi, lo) float split of Z (n x n float4) for the residual GEMMs
+  void* dinv = nullptr;        // complex64 factors: inverses of the 64 x 64 diagonal blocks of L, then of U
   double znorm_inf = 0.0;      // ||Z||_inf (FP64)
   int* d_status = nullptr;     // device status word
 };
@@ -184,13 +185,16 @@ fosb_status getrf_external_scratch(void* A, int64_t n, int64_t lda, int32_t* ipi
                                    int64_t max_ctas, cudaStream_t s);
 template <typename T>
 cudaError_t getrs(const void* LU, int64_t n, int64_t ldlu, const int32_t* ipiv, void* X, int64_t nrhs, int64_t ldx,
-                  cudaStream_t s, int* status = nullptr);
+                  cudaStream_t s, int* status = nullptr, const void* dinv = nullptr);
 // One whole triangular sweep with complex64 factors (unit lower if upper == 0, else upper
-// with its diagonal) for nrhs <= 8 right-hand sides stored dense (n x nrhs); scratch holds
+// with its diagonal) for nrhs <= 8 right-hand sides stored dense (n x nrhs), given the
+// inverses of the diagonal blocks (tri_block_inverses_c64); scratch holds
 // trsv_stream_scratch_ints(n) ints; a bounded wait that gives up sets *status.
 size_t trsv_stream_scratch_ints(int64_t n);
-cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, void* X, int64_t nrhs, int upper, int* scratch,
-                            int* status, cudaStream_t s);
+size_t tri_block_inverses_bytes(int64_t n);
+cudaError_t tri_block_inverses_c64(const void* LU, int64_t n, int64_t ld, void* Dinv, cudaStream_t s);
+cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, const void* Dinv, void* X, int64_t nrhs, int upper,
+                            int* scratch, int* status, cudaStream_t s);
 cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                 cudaStream_t s);
 cudaError_t convert_c64_to_c128(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,

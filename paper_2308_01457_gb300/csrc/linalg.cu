@@ -306,6 +306,84 @@ __global__ void split_ff_kernel(const double2* __restrict__ src, int64_t rows, i
   dst[i * ldd + j] = make_float4(rh, float(v.x - double(rh)), ih, float(v.y - double(ih)));
 }
 
+// Few right-hand sides (NC <= 8) on a pre-split A (op N): one warp per row, lanes stride
+// over k, float-float accumulation renormalised every 16 steps, then a float-float warp
+// reduction.  Streams the (hi, lo) split of A once: HBM-bound, where the FP64 row kernel is
+// bound by the FP64 pipe.
+__device__ __forceinline__ void ff_norm(float& h, float& l) {
+  const float s = h + l;
+  l = l - (s - h);
+  h = s;
+}
+__device__ __forceinline__ void ff_add_pair(float& h, float& l, float h2, float l2) {
+  const float s = h + h2;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (h2 - bb);
+  h = s;
+  l = l + l2 + e;
+  ff_norm(h, l);
+}
+template <int NC>
+__global__ void __launch_bounds__(256) zgemv_ff_kernel(int64_t M, int64_t K, double ar, double ai,
+                                                       const float4* __restrict__ A, int64_t lda,
+                                                       const float4* __restrict__ B, double beta,
+                                                       double2* __restrict__ C, int64_t ldc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row = int64_t(blockIdx.x) * 8 + warp;
+  if (row >= M) return;
+  float4 acc[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4* a = A + row * lda;
+  int step = 0;
+  for (int64_t k = lane; k < K; k += 32) {
+    const float4 av = __ldcs(a + k);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const float4 bv = __ldg(B + k * NC + j);
+      float4& c = acc[j];
+      ff_acc(c.x, c.y, av.x, av.y, bv.x, bv.y);
+      ff_acc(c.x, c.y, -av.z, -av.w, bv.z, bv.w);
+      ff_acc(c.z, c.w, av.x, av.y, bv.z, bv.w);
+      ff_acc(c.z, c.w, av.z, av.w, bv.x, bv.y);
+    }
+    if (++step == 16) {
+      step = 0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        ff_norm(acc[j].x, acc[j].y);
+        ff_norm(acc[j].z, acc[j].w);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    ff_norm(acc[j].x, acc[j].y);
+    ff_norm(acc[j].z, acc[j].w);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float h1 = __shfl_xor_sync(0xffffffffu, acc[j].x, off), l1 = __shfl_xor_sync(0xffffffffu, acc[j].y, off);
+      const float h2 = __shfl_xor_sync(0xffffffffu, acc[j].z, off), l2 = __shfl_xor_sync(0xffffffffu, acc[j].w, off);
+      ff_add_pair(acc[j].x, acc[j].y, h1, l1);
+      ff_add_pair(acc[j].z, acc[j].w, h2, l2);
+    }
+  }
+  if (lane < NC) {
+    float4 c = acc[0];
+#pragma unroll
+    for (int j = 1; j < NC; ++j)
+      if (lane == j) c = acc[j];
+    const double xr = double(c.x) + double(c.y), xi = double(c.z) + double(c.w);
+    double2 v = make_double2(ar * xr - ai * xi, ar * xi + ai * xr);
+    if (beta != 0.0) {
+      const double2 o = C[row * ldc + lane];
+      v.x += beta * o.x;
+      v.y += beta * o.y;
+    }
+    C[row * ldc + lane] = v;
+  }
+}
+
 // NJ complex columns per thread: tile 64 x 16 NJ (NJ = 4, or 3 for 33..48 right-hand sides)
 template <bool ATOMIC, int NJ>
 __global__ void __launch_bounds__(256) zgemm_ff_kernel(int opA, int opB, int64_t M, int64_t N, int64_t K, double ar,
@@ -1070,8 +1148,34 @@ cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, doub
                          cudaStream_t s, const void* A_split) {
   using V = double2;
   if (M <= 0 || N <= 0) return cudaSuccess;
-  // up to 8 right-hand sides: the FP64 row-per-warp kernel streams A once and is faster
-  // than a 64-wide tile that would be mostly padding
+  // up to 8 right-hand sides: a row-per-warp kernel that streams A once; float-float on the
+  // cached split of A when there is one, else FP64 (a 64-wide tile would be mostly padding)
+  if (K > 0 && opA == OP_N && opB == OP_N && N <= 8 && A_split) {
+    float4* bs = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&bs), size_t(K * N) * sizeof(float4), s);
+    if (e == cudaSuccess) e = split_ff(B, K, N, ldb, bs, N, s);
+    if (e == cudaSuccess) {
+      ProfScope prof("gemm_ff", s, 8.0 * double(M) * double(N) * double(K));
+      const float4* a4 = static_cast<const float4*>(A_split);
+      double2* c2 = static_cast<double2*>(C);
+      const unsigned g = cdiv(M, 8);
+#define FOSB_GEMV(NC) zgemv_ff_kernel<NC><<<g, 256, 0, s>>>(M, K, alpha_re, alpha_im, a4, lda, bs, beta, c2, ldc)
+      switch (N) {
+        case 1: FOSB_GEMV(1); break;
+        case 2: FOSB_GEMV(2); break;
+        case 3: FOSB_GEMV(3); break;
+        case 4: FOSB_GEMV(4); break;
+        case 5: FOSB_GEMV(5); break;
+        case 6: FOSB_GEMV(6); break;
+        case 7: FOSB_GEMV(7); break;
+        default: FOSB_GEMV(8); break;
+      }
+#undef FOSB_GEMV
+      e = launched();
+    }
+    if (bs) cudaFreeAsync(bs, s);
+    return e;
+  }
   if (K <= 0 || (opA == OP_N && N <= 8))
     return gemm<double>(opA, opB, M, N, K, alpha_re, alpha_im, A, lda, B, ldb, beta, C, ldc, s);
   if (cdiv(M, TBM) > 65535u) return cudaErrorInvalidValue;
@@ -1290,7 +1394,7 @@ template fosb_status getrf_external_scratch<float>(void*, int64_t, int64_t, int3
 // X <- Z^{-1} X given the factors (perm = composed row permutation, device).
 template <typename T>
 cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm, void* Xv, int64_t nrhs, int64_t ldx,
-                  cudaStream_t s, int* status) {
+                  cudaStream_t s, int* status, const void* dinv) {
   using V = typename C2<T>::type;
   const V* LU = static_cast<const V*>(LUv);
   V* X = static_cast<V*>(Xv);
@@ -1298,12 +1402,12 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(V) * n * nrhs, s);
   if (e != cudaSuccess) return e;
   gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
-  if (sizeof(T) == 4 && status && nrhs <= 8) {
+  if (sizeof(T) == 4 && status && dinv && nrhs <= 8) {
     // few right-hand sides: one persistent streaming kernel per sweep
     int* flags = nullptr;
     e = cudaMallocAsync(reinterpret_cast<void**>(&flags), sizeof(int) * trsv_stream_scratch_ints(n), s);
-    if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, tmp, nrhs, 0, flags, status, s);
-    if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, tmp, nrhs, 1, flags, status, s);
+    if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, dinv, tmp, nrhs, 0, flags, status, s);
+    if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, dinv, tmp, nrhs, 1, flags, status, s);
     if (flags) cudaFreeAsync(flags, s);
     if (e != cudaSuccess) return e;
     copy_kernel<V><<<cdiv(n * nrhs, 256), 256, 0, s>>>(tmp, n, nrhs, nrhs, X, ldx);
@@ -1354,9 +1458,9 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
 }
 
 template cudaError_t getrs<double>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t,
-                                   int*);
+                                   int*, const void*);
 template cudaError_t getrs<float>(const void*, int64_t, int64_t, const int32_t*, void*, int64_t, int64_t, cudaStream_t,
-                                  int*);
+                                  int*, const void*);
 
 cudaError_t convert_c128_to_c64(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                 cudaStream_t s) {
