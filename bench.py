@@ -51,7 +51,7 @@ FP64_PEAK_TFLOPS = 1.25
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
 # DRAM bytes (read + write) per complex64 output element of one tcgen05 LU-update launch,
 # from the ncu capture summarised in profiles/ (C is read and written once: 16 B algorithmic)
-LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (472.180480e6 + 403.065856e6) / 7616.0**2  # 15.09 B
+LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (471.830272e6 + 396.855296e6) / 7552.0**2  # 15.23 B
 
 
 def _peaks():
@@ -168,7 +168,7 @@ def run_fosb(args):
     timers = {}
     launches0 = F.lib().fosb_kernel_launches()
     clocks = _clock_sampler(local) if rank == 0 else None
-    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff"]
+    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz"]
     for fam in families:  # clear earlier records
         F.lib().fosb_profile_read(fam.encode(), None, None, None)
     F.lib().fosb_profile_enable(1)
@@ -221,8 +221,11 @@ def run_fosb(args):
                         if arith == F.ASM_FF else "27 algorithmic FP ops per point pair; FP64 nominal peak"),
         "gemm_ff": ("alu", 1.0, FP32_PEAK_TFLOPS, "zgemm_ff_kernel (float-float complex128 GEMM)",
                     "work = complex128 flops 8MNK executed as ~48 FP32 instructions per complex MAC"),
-        "lu_panel": ("latency", 1.0, None, "panel_smem_kernel<float> (cooperative, grid barrier per column)",
-                     "latency-bound: one grid barrier per column"),
+        "lu_panel": ("latency", 1.0, None, "tslu_gepp_kernel (tournament-pivoting panel)",
+                     "latency-bound: 64 sequential pivot steps per tree level"),
+        "gemm_oz": ("tensor", 1.0, bf16, "oz_gemm_kernel (bf16 digit-split tcgen05, FP64-class complex)",
+                    "work = complex128 flops 8MNK; executes 112 bf16 MMAs (28 digit pairs x 4) per complex product, "
+                    "so frac <= 8/(112 x 2)"),
     }
     dom = max((f for f in fam_model if fam_stats[f]["ms_per_step"] > 0),
               key=lambda f: fam_stats[f]["ms_per_step"], default="lu_update")
@@ -236,8 +239,9 @@ def run_fosb(args):
                 "peak_source": note + " (of measured)" if bound == "tensor" else note}
     if dom == "lu_update" and st["launches_per_step"] > 0:
         # DRAM bytes per launch from the ncu capture (bytes per output element of C, see
-        # profiles/), scaled to the average launch of the timed region (K = 64)
-        avg_outputs = st["work_per_step"] / (8.0 * 64.0 * st["launches_per_step"])
+        # profiles/), scaled to the average launch of the timed region: C elements = flops /
+        # (8 K) with K = 128, the depth of the trailing updates that carry most of the flops
+        avg_outputs = st["work_per_step"] / (8.0 * 128.0 * st["launches_per_step"])
         if LU_UPDATE_DRAM_BYTES_PER_OUTPUT is not None:
             roofline["traffic"] = round(LU_UPDATE_DRAM_BYTES_PER_OUTPUT * avg_outputs)
         roofline["algorithmic_bytes"] = round(16.0 * avg_outputs)
