@@ -107,6 +107,8 @@ struct fosb_lu_s {
   int64_t ldz = 0;
   void* zff = nullptr;         // MIXED: (hi, lo) float split of Z (n x n float4) for the residual GEMMs
   void* dinv = nullptr;        // complex64 factors: inverses of the 64 x 64 diagonal blocks of L, then of U
+  void* zdig = nullptr;        // MIXED: bf16 digit tiles of Z for the tensor-core residual GEMMs (oz_gemm)
+  int* zex = nullptr;          // MIXED: their row exponents
   double znorm_inf = 0.0;      // ||Z||_inf (FP64)
   int* d_status = nullptr;     // device status word
 };
@@ -168,6 +170,15 @@ cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int6
 cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im,
                          const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
                          cudaStream_t s, const void* A_split = nullptr);
+// FP64-class complex GEMM on the bf16 tensor cores by exact digit splitting (oz_gemm.cu):
+// oz_prepare_a writes the digit tiles (oz_a_bytes(M, K) bytes) and row exponents (M ints)
+// of the complex128 A (M x K, lda); oz_gemm then computes C <- beta C + alpha A B for a
+// complex128 B (K x N, ldb); a bounded wait that gives up sets *status.
+size_t oz_a_bytes(int64_t M, int64_t K);
+cudaError_t oz_prepare_a(const void* A, int64_t M, int64_t K, int64_t lda, void* digits, int* ex, cudaStream_t s);
+cudaError_t oz_gemm(int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im, const void* a_digits,
+                    const int* a_ex, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, int* status,
+                    cudaStream_t s);
 // dst (rows x cols float4, ldd) = (hi, lo) float split of the complex128 src
 cudaError_t split_ff(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                      cudaStream_t s);
