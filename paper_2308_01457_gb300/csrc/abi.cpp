@@ -107,8 +107,11 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   int it = 0;
   for (;;) {
     FOSB_CUDA(copy_matrix(Bsrc, n, nrhs, ldbs, r.p, nrhs, 16, s));
-    FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s,
-                           lu->zff));
+    if (lu->zdig && nrhs > 8)  // many right-hand sides: digit-split bf16 tensor cores
+      FOSB_CUDA(oz_gemm(n, nrhs, n, -1.0, 0.0, lu->zdig, lu->zex, X, ldx, 1.0, r.p, nrhs, lu->d_status, s));
+    else
+      FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s,
+                             lu->zff));
     FOSB_TRY(col_norms(r.p, n, nrhs, nrhs, nb.as<double>(), rn, s));
     FOSB_TRY(col_norms(X, n, nrhs, ldx, nb.as<double>(), xn, s));
     berr = 0.0;
@@ -220,6 +223,13 @@ fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu
     if ((e = cudaMalloc(&lu->zff, sizeof(float) * 4 * n * n)) != cudaSuccess ||
         (e = split_ff(Z, n, n, ldz, lu->zff, n, s)) != cudaSuccess)
       return cleanup(cuda_fail(e, "fosb_factor: split copy of Z"));
+    // and as exact bf16 digits for residuals with many right-hand sides (about 28 n^2 bytes)
+    if (n >= 256) {
+      if ((e = cudaMalloc(&lu->zdig, oz_a_bytes(n, n))) != cudaSuccess ||
+          (e = cudaMalloc(reinterpret_cast<void**>(&lu->zex), sizeof(int) * n)) != cudaSuccess ||
+          (e = oz_prepare_a(Z, n, n, ldz, lu->zdig, lu->zex, s)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "fosb_factor: digit tiles of Z"));
+    }
     Scratch nrm(s);
     if ((e = nrm.alloc(sizeof(double))) != cudaSuccess || (e = norm_inf_c128(Z, n, n, ldz, nrm.as<double>(), s)) ||
         (e = cudaMemcpyAsync(&lu->znorm_inf, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s)))
@@ -278,6 +288,8 @@ fosb_status fosb_lu_destroy(fosb_lu lu) {
   if (lu->d_status) cudaFree(lu->d_status);
   if (lu->zff) cudaFree(lu->zff);
   if (lu->dinv) cudaFree(lu->dinv);
+  if (lu->zdig) cudaFree(lu->zdig);
+  if (lu->zex) cudaFree(lu->zex);
   delete lu;
   return FOSB_OK;
 }

@@ -2,6 +2,8 @@
 seeded meshes.  Tolerances: Z and b entrywise relative to max|Z| (resp. max|b|) at
 1e-12 in FP64 (rounding only: same quadrature), 1e-5 in FP32; currents, far fields
 and covariances normwise at 1e-8 for FP64 and MIXED (refined), 1e-4 for FP32."""
+import math
+
 import numpy as np
 import pytest
 
@@ -181,6 +183,37 @@ def test_solve_multiple_rhs_and_ragged_sizes():
     B2 = B.clone()
     F.solve(lu, B2)
     assert _rel(B2.cpu().numpy(), Xo) < 1e-8
+
+
+def test_solve_many_rhs_ragged_digit_residual():
+    """More than 8 right-hand sides at N >= 256 put the refinement residuals on the
+    digit-split tensor-core product. N = 336 (torus 14 x 8) leaves a ragged 80-row tile
+    and a last 64-wide k chunk of one 16-wide step; 37 columns leave a ragged column tile."""
+    sm = S.torus(14, 8)
+    k = 1.7
+    m, om = _mesh(sm)
+    N = m.n_edges
+    assert N == 336
+    Z = torch.zeros((N, N), dtype=C128, device=DEV)
+    F.assemble_efie(m, k, Z)
+    rng = np.random.default_rng(7)
+    # columns of very different scales: the digits take one exponent per column
+    Bh = (rng.standard_normal((N, 37)) + 1j * rng.standard_normal((N, 37))) * 10.0 ** rng.uniform(-6, 6, 37)
+    B = torch.tensor(Bh, dtype=C128, device=DEV)
+    Xo = np.linalg.solve(O.assemble_z(om, k), Bh)
+    lu = F.factor(Z, prec=F.MIXED)
+    X = torch.zeros_like(B)
+    _, iters, berr = F.solve(lu, B, X)
+    Xg = X.cpu().numpy()
+    for c in range(37):
+        assert _rel(Xg[:, c], Xo[:, c]) < 1e-8, c
+    assert berr <= max(64.0, 8.0 * math.sqrt(N)) * 2.0**-52
+    # the FP64 residual of the returned solution, from an independent complex128 product
+    R = B - Z @ X
+    zn = Z.abs().sum(dim=1).max().item()
+    for c in range(37):
+        be = R[:, c].abs().max().item() / (zn * X[:, c].abs().max().item() + B[:, c].abs().max().item())
+        assert be <= 2.0 * max(64.0, 8.0 * math.sqrt(N)) * 2.0**-52, (c, be)
 
 
 @pytest.mark.parametrize("prec,tol", [("FP64", 1e-8), ("MIXED", 1e-8), ("FP32", 1e-4)])
