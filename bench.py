@@ -168,7 +168,8 @@ def run_fosb(args):
     timers = {}
     launches0 = F.lib().fosb_kernel_launches()
     clocks = _clock_sampler(local) if rank == 0 else None
-    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz"]
+    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "trsm_update",
+                "oz_prep", "getrs"]
     for fam in families:  # clear earlier records
         F.lib().fosb_profile_read(fam.encode(), None, None, None)
     F.lib().fosb_profile_enable(1)
@@ -226,14 +227,22 @@ def run_fosb(args):
         "gemm_oz": ("tensor", 1.0, bf16, "oz_gemm_kernel (bf16 digit-split tcgen05, FP64-class complex)",
                     "work = complex128 flops 8MNK; executes 112 bf16 MMAs (28 digit pairs x 4) per complex product, "
                     "so frac <= 8/(112 x 2)"),
+        "trsm_update": ("tensor", 1.0, tf32_peak, "cgemm_update_tc_ws_kernel in the blocked triangular sweeps (K = 64)",
+                        "sweep updates of solves with 16 or more right-hand sides; work = useful complex flops 8MNK"),
+        "oz_prep": ("hbm", 1.0, peaks.get("hbm_gbs", 6800.0), "oz_row_exp_kernel + oz_split_a_kernel (digit tiles of Z)",
+                    "work = bytes: 16 B read + 28 B of digits written per element of Z"),
+        # the whole triangular solve; it contains the trsm_update launches, so it is not a
+        # candidate for the dominant family
+        "getrs": ("latency", 1.0, None, "getrs (permutation, sweeps, copies)", "container of trsm_update"),
     }
-    dom = max((f for f in fam_model if fam_stats[f]["ms_per_step"] > 0),
+    dom = max((f for f in fam_model if fam_stats[f]["ms_per_step"] > 0 and f != "getrs"),
               key=lambda f: fam_stats[f]["ms_per_step"], default="lu_update")
     bound, wscale, peak, kname, note = fam_model[dom]
     st = fam_stats[dom]
-    achieved = st["work_per_step"] * wscale / (st["ms_per_step"] * 1e-3) / 1e12 if st["ms_per_step"] > 0 else 0.0
+    dom_scale, dom_unit = (1e9, "GB/s") if bound == "hbm" else (1e12, "TFLOP/s")
+    achieved = st["work_per_step"] * wscale / (st["ms_per_step"] * 1e-3) / dom_scale if st["ms_per_step"] > 0 else 0.0
     roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2) if peak else None,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None,
+                "unit": dom_unit, "frac": round(achieved / peak, 4) if peak else None,
                 "traffic": None, "kernel": kname, "family": dom,
                 "ms_per_step": round(st["ms_per_step"], 2), "launches_per_step": st["launches_per_step"],
                 "peak_source": note + " (of measured)" if bound == "tensor" else note}
@@ -248,9 +257,10 @@ def run_fosb(args):
     secondary = {}
     for f, (b, wsc, pk, kn, _) in fam_model.items():
         s_ = fam_stats[f]
-        rate = s_["work_per_step"] * wsc / (s_["ms_per_step"] * 1e-3) / 1e12 if s_["ms_per_step"] > 0 else 0.0
+        unit_scale, unit = (1e9, "GB/s") if b == "hbm" else (1e12, "TFLOP/s")
+        rate = s_["work_per_step"] * wsc / (s_["ms_per_step"] * 1e-3) / unit_scale if s_["ms_per_step"] > 0 else 0.0
         secondary[f] = {"ms_per_step": round(s_["ms_per_step"], 2), "launches_per_step": s_["launches_per_step"],
-                        "tflops": round(rate, 3), "frac": round(rate / pk, 4) if pk else None}
+                        "rate": round(rate, 3), "unit": unit, "frac": round(rate / pk, 4) if pk else None}
     # IR quality (refined path must reach FP64 backward error)
     berr = max(prob.levels[l].berr for l in prob.levels)
     e2e = run_e2e(args, W, meshes, dirs, arith) if (rank == 0 and not args.no_e2e) else None

@@ -162,9 +162,10 @@ template <typename T>
 cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im, const void* A,
                  int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s);
 // C (M x N) -= A (M x K) B (K x N), complex64 row-major, tcgen05 tensor cores with 3xTF32;
-// a bounded mbarrier wait that gives up sets *status = FOSB_ERR_TIMEOUT
+// a bounded mbarrier wait that gives up sets *status = FOSB_ERR_TIMEOUT.  family names the
+// timing record (fosb_profile_read): factor updates and solve sweeps are timed apart
 cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
-                            void* C, int64_t ldc, int* status, cudaStream_t s);
+                            void* C, int64_t ldc, int* status, cudaStream_t s, const char* family = "lu_update");
 // complex128 GEMM computed in float-float on the FP32 pipe (FP64-class accuracy).  A_split,
 // if given, is split_ff of A as stored (same shape, leading dimension lda).
 cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im,

@@ -1399,6 +1399,7 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   const V* LU = static_cast<const V*>(LUv);
   V* X = static_cast<V*>(Xv);
   V* tmp = nullptr;
+  ProfScope prof("getrs", s, 8.0 * double(n) * double(n) * double(nrhs));
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(V) * n * nrhs, s);
   if (e != cudaSuccess) return e;
   gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
@@ -1432,7 +1433,7 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
     if (rest > 0) {
       if (sizeof(T) == 4 && status && nrhs >= 16)  // wide right-hand sides: tensor cores
         e = cgemm_update_tc(rest, nrhs, ib, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs,
-                            tmp + (i0 + ib) * nrhs, nrhs, status, s);
+                            tmp + (i0 + ib) * nrhs, nrhs, status, s, "trsm_update");
       else
         e = gemm<T>(OP_N, OP_N, rest, nrhs, ib, -1.0, 0.0, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs,
                     1.0, tmp + (i0 + ib) * nrhs, nrhs, s);
@@ -1446,7 +1447,7 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
     diag(i0, ib, 1);
     if (i0 > 0) {
       if (sizeof(T) == 4 && status && nrhs >= 16)
-        e = cgemm_update_tc(i0, nrhs, ib, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, tmp, nrhs, status, s);
+        e = cgemm_update_tc(i0, nrhs, ib, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, tmp, nrhs, status, s, "trsm_update");
       else
         e = gemm<T>(OP_N, OP_N, i0, nrhs, ib, -1.0, 0.0, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0, tmp, nrhs, s);
       if (e != cudaSuccess) return e;

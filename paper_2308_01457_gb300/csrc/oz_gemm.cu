@@ -1,9 +1,10 @@
 // FP64-class complex GEMM C <- beta C + alpha Z X on the bf16 tensor cores by exact digit
 // splitting, for the refinement residuals of multi-right-hand-side solves (A6, A9).
 //
-// Every row i of Z is scaled by a power of two sigma_i >= its largest |Re|, |Im| and written
-// as seven signed base-256 digits:  Z_ik = sigma_i 2^-7 sum_{s=0..6} 2^{-8s} d_s[i,k],
-// |d_s| <= 128 (round to nearest at each digit), so each digit is exact in bf16; the same
+// Every row i of Z is scaled by a power of two sigma_i > its largest |Re|, |Im| and written
+// as seven signed base-256 digits:  Z_ik = sigma_i 2^-7 sum_{s=0..6} 2^{-8s} d_s[i,k] up to
+// 2^-56 sigma_i (the balanced base-256 form of Z_ik 2^55 / sigma_i rounded to an integer),
+// |d_s| <= 128, so each digit is exact in bf16; the same
 // for every column j of X with tau_j and digits e_t.  Then
 //   (Z X)_ij = sigma_i tau_j 2^-14 sum_{s,t} 2^{-8(s+t)} sum_k d_s[i,k] e_t[k,j],
 // and a digit product is an integer of at most 2^14, so sums of the same order g = s+t over
@@ -110,109 +111,132 @@ __device__ __forceinline__ void oz_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 // ---------------------------------------------------------------- digit splitting
-// Power-of-two scale exponent per row of a complex128 matrix (rows x cols, ld): the
-// smallest e with max_k max(|Re|, |Im|) <= 2^e (e = 0 for a zero row).  One warp per row.
+// |x| as an ordered integer: the bit pattern with the sign cleared (non-negative doubles
+// compare like their bit patterns), so the maxima below run on the integer pipe.
+__device__ __forceinline__ unsigned long long oz_abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+// the smallest e with |x| < 2^e for the largest |x| of a row or column (bit pattern mb),
+// e = 0 for zero: m = f 2^e with f in [0.5, 1)
+__device__ __forceinline__ int oz_exponent(unsigned long long mb) {
+  int e = 0;
+  if (mb) frexp(__longlong_as_double(static_cast<long long>(mb)), &e);
+  return e;
+}
+__device__ __forceinline__ unsigned long long oz_umax(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+// Power-of-two scale exponent per row of a complex128 matrix (rows x cols, ld), the max
+// over Re and Im parts.  One warp per row.
 __global__ void oz_row_exp_kernel(const double2* __restrict__ A, int64_t rows, int64_t cols, int64_t ld,
                                   int* __restrict__ ex) {
   const int64_t row = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  double m = 0.0;
+  unsigned long long m = 0;
+  const double2* a = A + row * ld;
+#pragma unroll 4
   for (int64_t k = lane; k < cols; k += 32) {
-    const double2 v = A[row * ld + k];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const double2 v = a[k];
+    m = oz_umax(m, oz_umax(oz_abs_bits(v.x), oz_abs_bits(v.y)));
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-  if (lane == 0) {
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);  // m = f 2^e with f in [0.5, 1): m <= 2^e
-    ex[row] = e;
-  }
+  for (int off = 16; off > 0; off >>= 1) m = oz_umax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if (lane == 0) ex[row] = oz_exponent(m);
 }
 // the same per column of a matrix stored rows x cols (exponent per column)
 __global__ void oz_col_exp_kernel(const double2* __restrict__ A, int64_t rows, int64_t cols, int64_t ld,
                                   int* __restrict__ ex) {
   const int64_t col = blockIdx.x;
-  __shared__ double red[8];
-  double m = 0.0;
+  __shared__ unsigned long long red[8];
+  unsigned long long m = 0;
   for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
     const double2 v = A[r * ld + col];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    m = oz_umax(m, oz_umax(oz_abs_bits(v.x), oz_abs_bits(v.y)));
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  for (int off = 16; off > 0; off >>= 1) m = oz_umax(m, __shfl_xor_sync(0xffffffffu, m, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);
-    ex[col] = e;
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = oz_umax(m, red[w]);
+    ex[col] = oz_exponent(m);
   }
 }
-__device__ __forceinline__ void oz_digits(double x, int e, float (&d)[OZ_ND]) {
-  double u = ldexp(x, 7 - e);  // |u| <= 128
+// x 2^(55 - e) rounded to an integer (|x| < 2^e, so |F| <= 2^55), from the bit pattern:
+// x = M 2^(b - 1075) with the 53-bit significand M (b the biased exponent; subnormals have
+// b = 1 and no hidden bit), so F = M 2^(b - 1020 - e), a left shift of at most 2 or a right
+// shift rounded to nearest (ties away from zero).  Everything below 2^-1 of the last digit
+// is dropped here, the same truncation as seven successive digit roundings.
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  int b = int((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (b) m |= 1ull << 52;
+  else b = 1;
+  const int sh = b - 1020 - e;
+  unsigned long long f;
+  if (sh >= 0) f = m << sh;
+  else if (sh >= -60) f = (m + (1ull << (-sh - 1))) >> (-sh);
+  else f = 0;
+  return (bits >> 63) ? -static_cast<long long>(f) : static_cast<long long>(f);
+}
+// bf16 bit pattern of (byte - 128) for an integer byte in [0, 256]: the float 2^23 + byte
+// minus 2^23 + 128 is exact, and a float holding an integer of magnitude <= 256 has its
+// nonzero bits in the top 16
+__device__ __forceinline__ uint32_t oz_bf16_bits(uint32_t byte) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | byte) - 8388736.0f) >> 16;
+}
+// Digit tiles of a matrix read as rows x K elements (element (r, k) at A[r * rs + k * ks]),
+// one power-of-two exponent per row, zero-padded to whole tiles of TR rows x 16 k:
+// tile (rt, kc, s, p) of TR x 16 bf16 at byte offset (((rt * KC + kc) * 7 + s) * 2 + p) * TR * 32.
+// Z (rs = ld, ks = 1, TR = 128) and X read by columns (rs = 1, ks = ld, TR = 32) both land here.
+// Digits: F = x 2^(55 - e) rounded (above) is written in balanced base 256,
+// F = sum_{s=0..6} d_s 256^(6-s) with d_1..d_6 in [-128, 127] and |d_0| <= 128: adding 128 in
+// each of the seven byte positions turns every digit into a plain byte (the carries of the
+// balanced form are those of the addition), so d_s = byte_{6-s}(F + 0x80...80) - 128.
+// A thread owns 8 consecutive k of one row, one 16-byte row of a core matrix, and writes it
+// for every digit and part with one vector store; a warp covers 8 rows x 4 such groups, so
+// each store instruction fills two whole 256-byte segments.
+template <int TR>
+__global__ void oz_split_kernel(const double2* __restrict__ A, int64_t rows, int64_t K, int64_t rs, int64_t ks,
+                                const int* __restrict__ ex, int64_t KC, unsigned char* __restrict__ out) {
+  constexpr int TILE = TR * OZ_KS * 2;
+  constexpr unsigned long long BIAS = 0x0080808080808080ull;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = int64_t(blockIdx.y) * 8 + (lane & 7);
+  const int64_t kg = (int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4 + (lane >> 3);
+  if (kg >= KC * 2) return;
+  const int e = row < rows ? ex[row] : 0;
+  unsigned long long gr[8], gi[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t k = kg * 8 + j;
+    gr[j] = gi[j] = BIAS;
+    if (row < rows && k < K) {
+      const double2 v = A[row * rs + k * ks];
+      gr[j] = static_cast<unsigned long long>(oz_fixed(v.x, e)) + BIAS;
+      gi[j] = static_cast<unsigned long long>(oz_fixed(v.y, e)) + BIAS;
+    }
+  }
+  const int64_t rt = row / TR, kc = kg >> 1;
+  unsigned char* base = out + ((rt * KC + kc) * OZ_NT) * TILE + oz_off(int(row % TR), int(kg & 1) * 8);
 #pragma unroll
   for (int s = 0; s < OZ_ND; ++s) {
-    const double q = rint(u);
-    d[s] = float(q);
-    u = (u - q) * 256.0;  // exact: |u - q| <= 1/2
+    const int sh = 8 * (6 - s);
+    uint32_t pr[4], pi[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // byte 6 (digit 0) may be 256: take it with the bits above
+      const uint32_t msk = s == 0 ? 0x1FFu : 0xFFu;
+      pr[j] = oz_bf16_bits(uint32_t(gr[2 * j] >> sh) & msk) | (oz_bf16_bits(uint32_t(gr[2 * j + 1] >> sh) & msk) << 16);
+      pi[j] = oz_bf16_bits(uint32_t(gi[2 * j] >> sh) & msk) | (oz_bf16_bits(uint32_t(gi[2 * j + 1] >> sh) & msk) << 16);
+    }
+    *reinterpret_cast<uint4*>(base + (s * 2 + 0) * TILE) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+    *reinterpret_cast<uint4*>(base + (s * 2 + 1) * TILE) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
   }
 }
-// Digit tiles of Z (the A operand, rows x K, row exponents), zero-padded to whole tiles:
-// tile (rt, kc, s, p) of 128 rows x 16 k at byte offset (((rt * KC + kc) * 7 + s) * 2 + p) * 4096.
-// One thread per (row, k) of the padded range.
-__global__ void oz_split_a_kernel(const double2* __restrict__ A, int64_t rows, int64_t K, int64_t ld,
-                                  const int* __restrict__ ex, int64_t KC, unsigned char* __restrict__ out) {
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t row = blockIdx.y;
-  if (k >= KC * OZ_KS) return;
-  float dr[OZ_ND], di[OZ_ND];
-  if (row < rows && k < K) {
-    const double2 v = A[row * ld + k];
-    const int e = ex[row];
-    oz_digits(v.x, e, dr);
-    oz_digits(v.y, e, di);
-  } else {
-#pragma unroll
-    for (int s = 0; s < OZ_ND; ++s) dr[s] = di[s] = 0.f;
-  }
-  const int64_t rt = row / OZ_TM, kc = k / OZ_KS;
-  const int off = oz_off(int(row % OZ_TM), int(k % OZ_KS));
-  unsigned char* base = out + ((rt * KC + kc) * OZ_ND) * 2 * OZ_ATILE;
-#pragma unroll
-  for (int s = 0; s < OZ_ND; ++s) {
-    *reinterpret_cast<__nv_bfloat16*>(base + (s * 2 + 0) * OZ_ATILE + off) = __float2bfloat16_rn(dr[s]);
-    *reinterpret_cast<__nv_bfloat16*>(base + (s * 2 + 1) * OZ_ATILE + off) = __float2bfloat16_rn(di[s]);
-  }
-}
-// Digit tiles of X (the B operand, K x cols row-major, column exponents), K-major per
-// column: tile (ct, kc, t, p) of 32 columns x 16 k at (((ct * KC + kc) * 7 + t) * 2 + p) * 1024.
-__global__ void oz_split_b_kernel(const double2* __restrict__ X, int64_t K, int64_t cols, int64_t ld,
-                                  const int* __restrict__ ex, int64_t KC, unsigned char* __restrict__ out) {
-  const int64_t col = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // padded column
-  const int64_t k = blockIdx.y;                                         // padded k
-  if (col >= ((cols + OZ_TN - 1) / OZ_TN) * OZ_TN) return;
-  float dr[OZ_ND], di[OZ_ND];
-  if (col < cols && k < K) {
-    const double2 v = X[k * ld + col];
-    const int e = ex[col];
-    oz_digits(v.x, e, dr);
-    oz_digits(v.y, e, di);
-  } else {
-#pragma unroll
-    for (int s = 0; s < OZ_ND; ++s) dr[s] = di[s] = 0.f;
-  }
-  const int64_t ct = col / OZ_TN, kc = k / OZ_KS;
-  const int off = oz_off(int(col % OZ_TN), int(k % OZ_KS));
-  unsigned char* base = out + ((ct * KC + kc) * OZ_ND) * 2 * OZ_BTILE;
-#pragma unroll
-  for (int s = 0; s < OZ_ND; ++s) {
-    *reinterpret_cast<__nv_bfloat16*>(base + (s * 2 + 0) * OZ_BTILE + off) = __float2bfloat16_rn(dr[s]);
-    *reinterpret_cast<__nv_bfloat16*>(base + (s * 2 + 1) * OZ_BTILE + off) = __float2bfloat16_rn(di[s]);
-  }
-}
+constexpr int OZ_SPLIT_WARPS = 8;  // a block covers 8 rows x 8 warps x 4 groups x 8 k = 8 x 256
 
 // ---------------------------------------------------------------- the product
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -425,10 +449,11 @@ size_t oz_a_bytes(int64_t M, int64_t K) {
 cudaError_t oz_prepare_a(const void* A, int64_t M, int64_t K, int64_t lda, void* digits, int* ex, cudaStream_t s) {
   if (M <= 0 || K <= 0) return cudaSuccess;
   const int64_t KC = (K + OZ_KS - 1) / OZ_KS, MP = ((M + OZ_TM - 1) / OZ_TM) * OZ_TM;
-  if (MP > 65535) return cudaErrorInvalidValue;
+  if (MP / 8 > 65535) return cudaErrorInvalidValue;
+  ProfScope prof("oz_prep", s, 44.0 * double(M) * double(K));  // bytes read + written
   oz_row_exp_kernel<<<oz_cdiv(M, 8), 256, 0, s>>>(static_cast<const double2*>(A), M, K, lda, ex);
-  oz_split_a_kernel<<<dim3(oz_cdiv(KC * OZ_KS, 128), unsigned(MP)), 128, 0, s>>>(
-      static_cast<const double2*>(A), M, K, lda, ex, KC, static_cast<unsigned char*>(digits));
+  oz_split_kernel<OZ_TM><<<dim3(oz_cdiv(KC * 2, OZ_SPLIT_WARPS * 4), unsigned(MP / 8)), OZ_SPLIT_WARPS * 32, 0, s>>>(
+      static_cast<const double2*>(A), M, K, lda, 1, ex, KC, static_cast<unsigned char*>(digits));
   return launched(2);
 }
 
@@ -449,7 +474,7 @@ cudaError_t oz_gemm(int64_t M, int64_t N, int64_t K, double alpha_re, double alp
     attr[dev] = true;
   }
   const int64_t KC = (K + OZ_KS - 1) / OZ_KS, CT = (N + OZ_TN - 1) / OZ_TN;
-  if (KC * OZ_KS > 65535) return cudaErrorInvalidValue;
+  if (CT * OZ_TN / 8 > 65535) return cudaErrorInvalidValue;
   const size_t bbytes = size_t(CT) * size_t(KC) * OZ_NT * OZ_BTILE;
   unsigned char* bd = nullptr;
   int* bex = nullptr;
@@ -457,8 +482,8 @@ cudaError_t oz_gemm(int64_t M, int64_t N, int64_t K, double alpha_re, double alp
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&bex), sizeof(int) * size_t(N), s);
   if (e == cudaSuccess) {
     oz_col_exp_kernel<<<unsigned(N), 256, 0, s>>>(static_cast<const double2*>(B), K, N, ldb, bex);
-    oz_split_b_kernel<<<dim3(oz_cdiv(CT * OZ_TN, 128), unsigned(KC * OZ_KS)), 128, 0, s>>>(
-        static_cast<const double2*>(B), K, N, ldb, bex, KC, bd);
+    oz_split_kernel<OZ_TN><<<dim3(oz_cdiv(KC * 2, OZ_SPLIT_WARPS * 4), unsigned(CT * OZ_TN / 8)), OZ_SPLIT_WARPS * 32,
+                             0, s>>>(static_cast<const double2*>(B), N, K, 1, ldb, bex, KC, bd);
     const int64_t tiles = ((M + OZ_TM - 1) / OZ_TM) * CT;
     const unsigned grid = unsigned(std::min<int64_t>(tiles, std::max(nsm[dev], 1)));
     ProfScope prof("gemm_oz", s, 8.0 * double(M) * double(N) * double(K));

@@ -370,7 +370,7 @@ inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
 // C (M x N) -= A (M x K) B (K x N), complex64 row-major, on tcgen05 (3xTF32).
 cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
-                            void* C, int64_t ldc, int* status, cudaStream_t s) {
+                            void* C, int64_t ldc, int* status, cudaStream_t s, const char* family) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   static bool attr[64] = {};
   static int nsm[64] = {};
@@ -388,7 +388,7 @@ cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int6
   const unsigned grid = unsigned(std::min<int64_t>(tiles, std::max(nsm[dev], 1)));  // persistent: one CTA per SM
   // 16-byte epilogue accesses need a 16-byte aligned C with an even leading dimension
   const int vec_ok = (reinterpret_cast<uintptr_t>(C) % 16 == 0) && (ldc % 2 == 0);
-  ProfScope prof("lu_update", s, 8.0 * double(M) * double(N) * double(K));
+  ProfScope prof(family, s, 8.0 * double(M) * double(N) * double(K));
   cgemm_update_tc_ws_kernel<<<grid, WS_THREADS, WS_SMEM, s>>>(M, N, K, static_cast<const float2*>(A), lda,
                                                              static_cast<const float2*>(B), ldb,
                                                              static_cast<float2*>(C), ldc, status, vec_ok);
