@@ -107,7 +107,7 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   int it = 0;
   for (;;) {
     FOSB_CUDA(copy_matrix(Bsrc, n, nrhs, ldbs, r.p, nrhs, 16, s));
-    if (lu->zdig && nrhs > 8)  // many right-hand sides: digit-split bf16 tensor cores
+    if (lu->zdig && nrhs > 4)  // 5 or more right-hand sides: digit-split bf16 tensor cores
       FOSB_CUDA(oz_gemm(n, nrhs, n, -1.0, 0.0, lu->zdig, lu->zex, X, ldx, 1.0, r.p, nrhs, lu->d_status, s));
     else
       FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, nrhs, n, -1.0, 0.0, lu->zref, lu->ldz, X, ldx, 1.0, r.p, nrhs, s,

@@ -199,10 +199,11 @@ template <typename T>
 cudaError_t getrs(const void* LU, int64_t n, int64_t ldlu, const int32_t* ipiv, void* X, int64_t nrhs, int64_t ldx,
                   cudaStream_t s, int* status = nullptr, const void* dinv = nullptr);
 // One whole triangular sweep with complex64 factors (unit lower if upper == 0, else upper
-// with its diagonal) for nrhs <= 8 right-hand sides stored dense (n x nrhs), given the
-// inverses of the diagonal blocks (tri_block_inverses_c64); scratch holds
-// trsv_stream_scratch_ints(n) ints; a bounded wait that gives up sets *status.
-size_t trsv_stream_scratch_ints(int64_t n);
+// with its diagonal) for nrhs <= kTrsvStreamMaxRhs right-hand sides stored dense
+// (n x nrhs), given the inverses of the diagonal blocks (tri_block_inverses_c64); scratch
+// holds trsv_stream_scratch_ints(n, nrhs) ints; a bounded wait that gives up sets *status.
+constexpr int64_t kTrsvStreamMaxRhs = 1024;
+size_t trsv_stream_scratch_ints(int64_t n, int64_t nrhs);
 size_t tri_block_inverses_bytes(int64_t n);
 cudaError_t tri_block_inverses_c64(const void* LU, int64_t n, int64_t ld, void* Dinv, cudaStream_t s);
 cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, const void* Dinv, void* X, int64_t nrhs, int upper,

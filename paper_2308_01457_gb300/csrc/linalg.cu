@@ -1403,10 +1403,10 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(V) * n * nrhs, s);
   if (e != cudaSuccess) return e;
   gather_rows_kernel<T><<<cdiv(n * nrhs, 256), 256, 0, s>>>(X, ldx, perm, n, nrhs, tmp, nrhs);
-  if (sizeof(T) == 4 && status && dinv && nrhs <= 8) {
-    // few right-hand sides: one persistent streaming kernel per sweep
+  if (sizeof(T) == 4 && status && dinv && nrhs <= kTrsvStreamMaxRhs) {
+    // one persistent streaming kernel per sweep
     int* flags = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void**>(&flags), sizeof(int) * trsv_stream_scratch_ints(n), s);
+    e = cudaMallocAsync(reinterpret_cast<void**>(&flags), sizeof(int) * trsv_stream_scratch_ints(n, nrhs), s);
     if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, dinv, tmp, nrhs, 0, flags, status, s);
     if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, dinv, tmp, nrhs, 1, flags, status, s);
     if (flags) cudaFreeAsync(flags, s);

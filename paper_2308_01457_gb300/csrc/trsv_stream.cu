@@ -1,16 +1,17 @@
-// Streaming triangular solves with complex64 factors for a few right-hand sides (A6: the
-// forward and backward sweeps L y = P b, U x = y of every refined solve).
+// Streaming triangular solves with complex64 factors (A6: the forward and backward sweeps
+// L y = P b, U x = y of every refined solve, and of the multi-right-hand-side covariance solves).
 //
 // A blocked sweep that launches one diagonal solve and one panel update per 64-row block
-// is latency-bound for one right-hand side (2 x n/64 dependent launches per sweep).  Here
-// one persistent kernel does a whole sweep: CTAs take 64-row blocks in order from a ticket
-// counter; the CTA of block i accumulates L_ij y_j (U_ij x_j for the backward sweep) over
-// the blocks j that precede it in the sweep as each one is published, then solves its
-// diagonal block (a 64 x 64 product with its precomputed inverse) and publishes y_i
-// through flags[i].  A block
-// only waits for blocks that were taken earlier, by CTAs that are running or done, so the
-// waits always end; each is bounded anyway and a time-out sets the status word, which every
-// waiter polls, so the sweep ends quickly and the host reports FOSB_ERR_TIMEOUT.
+// is latency-bound (2 x n/64 dependent launches per sweep).  Here one persistent kernel
+// does a whole sweep.  The right-hand sides are cut into chunks of at most 16 columns (one
+// chunk of the exact width for 1-8); CTAs take (block, chunk) tasks in block-major order
+// from a ticket counter.  The CTA of task (i, c) accumulates L_ij y_j (U_ij x_j for the
+// backward sweep) over the blocks j that precede i in the sweep as chunk c of each one is
+// published, then solves its diagonal block (a 64 x 64 product with its precomputed
+// inverse) and publishes chunk c of y_i through flags[i * chunks + c].  A task only waits
+// for tasks that were taken earlier, by CTAs that are running or done, so the waits always
+// end; each is bounded anyway and a time-out sets the status word, which every waiter
+// polls, so the sweep ends quickly and the host reports FOSB_ERR_TIMEOUT.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -99,47 +100,100 @@ __global__ void __launch_bounds__(256) tri_block_inverse_kernel(const float2* __
   }
 }
 
+// Shared tiles of the streaming sweep.  A factor tile (and, after the panel product, the
+// inverse of the diagonal block) is 64 x 64 with a row pitch of 72 complex values; the
+// published block of the solution is 64 x NR with an odd pitch NRP.  Thread (g, q) of 256
+// owns rows g and g + 32 and the columns q, q + 8, ..., q + 56, so in one step of c the 16
+// threads of a half-warp read 8 consecutive complex values of two rows 72 apart (every bank
+// once) and 8 values of the solution block 2 NRP words apart (distinct banks, NRP odd).
+constexpr int kLP = 72;
 template <int NR>
-__global__ void __launch_bounds__(256) trsv_stream_kernel(const float2* __restrict__ LU, int64_t n, int64_t ld,
-                                                          const float2* __restrict__ Dinv, float2* X, int upper,
-                                                          int* ticket, int* flags, int* status) {
-  __shared__ float2 sY[kTB][NR];          // the published block being consumed
-  __shared__ float2 sR[kTB][NR];          // this block's right-hand side after the panel product
-  __shared__ float2 sDi[kTB][kTB + 1];    // inverse of this block's diagonal block
-  __shared__ long long s_blk;
+struct StreamSmem {
+  static constexpr int NRP = NR | 1;
+  float2 L[kTB][kLP];
+  float2 Y[kTB][NRP];
+};
+
+// acc0/acc1 (rows g, g + 32) += T[rows][cols] Y[cols][0..NR) over this thread's 8 columns
+template <int NR>
+__device__ __forceinline__ void stream_tile_product(const StreamSmem<NR>& sm, int g, int q, float2 (&acc0)[NR],
+                                                    float2 (&acc1)[NR]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cc = q + 8 * c;
+    const float2 l0 = sm.L[g][cc], l1 = sm.L[g + 32][cc];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const float2 y = sm.Y[cc][k];
+      cfma(acc0[k], l0, y);
+      cfma(acc1[k], l1, y);
+    }
+  }
+}
+// sum over the 8 column owners q (lanes differing in their low three bits)
+template <int NR>
+__device__ __forceinline__ void stream_reduce_q(float2 (&a)[NR]) {
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+      a[k].x += __shfl_xor_sync(0xffffffffu, a[k].x, off);
+      a[k].y += __shfl_xor_sync(0xffffffffu, a[k].y, off);
+    }
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256, 2) trsv_stream_kernel(const float2* __restrict__ LU, int64_t n, int64_t ld,
+                                                          const float2* __restrict__ Dinv, float2* X, int64_t ldx,
+                                                          int nrhs, int chunks, int upper, int* ticket, int* flags,
+                                                          int* status) {
+  extern __shared__ float4 stream_raw[];
+  StreamSmem<NR>& sm = *reinterpret_cast<StreamSmem<NR>*>(stream_raw);
+  __shared__ long long s_task;
   __shared__ int s_abort;
-  const int t = threadIdx.x;
-  const int r = t >> 2, q = t & 3;        // row r of the block, columns q*16 .. q*16+15
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int g = t >> 3, q = t & 7;
   const int64_t nblk = (n + kTB - 1) / kTB;
   for (;;) {
     if (t == 0) {
-      s_blk = atomicAdd(ticket, 1);
+      s_task = atomicAdd(ticket, 1);
       s_abort = 0;
     }
     __syncthreads();
-    const int64_t b = s_blk;
+    const int64_t task = s_task;
+    const int64_t b = task / chunks;
+    const int ch = int(task % chunks);
     if (b >= nblk) break;
     const int64_t ib = upper ? nblk - 1 - b : b;
     const int64_t r0 = ib * kTB;
     const int rows = int(std::min<int64_t>(kTB, n - r0));
-    for (int e = t; e < kTB * kTB; e += blockDim.x) sDi[e / kTB][e % kTB] = Dinv[ib * kTB * kTB + e];
-    float2 acc[NR];
+    const int k0 = ch * NR, nc = std::min(NR, nrhs - k0);  // this chunk's columns of X
+    float2 acc0[NR], acc1[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int k = 0; k < NR; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
     const int64_t jcount = upper ? nblk - 1 - ib : ib;
+    // factor tile of block jj in registers: warp w holds rows 8w .. 8w+7, lanes the columns
+    // lane and lane + 32 (256 contiguous bytes of a row per load instruction)
+    float2 lreg[16];
+    auto fetch = [&](int64_t jj) {
+      const int64_t c0 = (upper ? nblk - 1 - jj : jj) * kTB;
+      const int cols = int(std::min<int64_t>(kTB, n - c0));
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rr = warp * 8 + i;
+        const float2* src = LU + (r0 + rr) * ld + c0;
+        lreg[2 * i] = (rr < rows && lane < cols) ? __ldg(src + lane) : make_float2(0.f, 0.f);
+        lreg[2 * i + 1] = (rr < rows && lane + 32 < cols) ? __ldg(src + lane + 32) : make_float2(0.f, 0.f);
+      }
+    };
+    if (jcount > 0) fetch(0);
     for (int64_t jj = 0; jj < jcount; ++jj) {
       const int64_t jb = upper ? nblk - 1 - jj : jj;  // in publication order
       const int64_t c0 = jb * kTB;
       const int cols = int(std::min<int64_t>(kTB, n - c0));
-      // this thread's 16 factor entries do not depend on the block being waited for
-      float2 lreg[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int cc = q * 16 + c;
-        lreg[c] = (r < rows && cc < cols) ? __ldg(LU + (r0 + r) * ld + c0 + cc) : make_float2(0.f, 0.f);
-      }
       if (t == 0) {
-        const volatile int* f = flags + jb;
+        const volatile int* f = flags + jb * chunks + ch;
         long long spins = 0;
         while (*f == 0) {
           if (++spins > kFlagSpinLimit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
@@ -151,73 +205,80 @@ __global__ void __launch_bounds__(256) trsv_stream_kernel(const float2* __restri
         }
         __threadfence();
       }
-      __syncthreads();  // also: every thread is done with sY of the previous block
+      __syncthreads();  // also: every thread is done with the tiles of the previous block
       if (s_abort) break;
-      for (int e = t; e < cols * NR; e += blockDim.x) sY[e / NR][e % NR] = __ldcg(X + (c0 + e / NR) * NR + e % NR);
-      __syncthreads();
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int cc = q * 16 + c;
-        if (cc < cols) {
-#pragma unroll
-          for (int k = 0; k < NR; ++k) cfma(acc[k], lreg[c], sY[cc][k]);
-        }
+      for (int i = 0; i < 8; ++i) {
+        sm.L[warp * 8 + i][lane] = lreg[2 * i];
+        sm.L[warp * 8 + i][lane + 32] = lreg[2 * i + 1];
       }
+      for (int e = t; e < kTB * NR; e += blockDim.x) {
+        const int rr = e / NR, k = e % NR;
+        sm.Y[rr][k] = (rr < cols && k < nc) ? __ldcg(X + (c0 + rr) * ldx + k0 + k) : make_float2(0.f, 0.f);
+      }
+      if (jj + 1 < jcount) fetch(jj + 1);  // in flight during the product below
+      __syncthreads();
+      stream_tile_product<NR>(sm, g, q, acc0, acc1);
     }
-    if (s_abort) {  // every later wait gives up at once; this block stays unpublished
+    if (s_abort) {  // every later wait gives up at once; this task stays unpublished
       __syncthreads();
       continue;
     }
-    // reduce the four column quarters of each row; right-hand side of the diagonal block
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, 1);
-      acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, 1);
-      acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, 2);
-      acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, 2);
-    }
+    // right-hand side of the diagonal block: r = x - sum_j L_ij y_j
+    stream_reduce_q<NR>(acc0);
+    stream_reduce_q<NR>(acc1);
+    __syncthreads();  // every thread is done with the last factor tile
     if (q == 0) {
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        float2 v = make_float2(0.f, 0.f);
-        if (r < rows) {
-          const float2 x = X[(r0 + r) * NR + k];
-          v = make_float2(x.x - acc[k].x, x.y - acc[k].y);
+        float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+        if (k < nc) {
+          if (g < rows) {
+            const float2 x = X[(r0 + g) * ldx + k0 + k];
+            v0 = make_float2(x.x - acc0[k].x, x.y - acc0[k].y);
+          }
+          if (g + 32 < rows) {
+            const float2 x = X[(r0 + g + 32) * ldx + k0 + k];
+            v1 = make_float2(x.x - acc1[k].x, x.y - acc1[k].y);
+          }
         }
-        sR[r][k] = v;
+        sm.Y[g][k] = v0;
+        sm.Y[g + 32][k] = v1;
       }
     }
+    const float2* D = Dinv + ib * kTB * kTB;
+    for (int e = t; e < kTB * kTB; e += blockDim.x) sm.L[e / kTB][e % kTB] = D[e];
     __syncthreads();
-    // y = Dinv r: row r, quarter q of the columns, then the same quarter reduction
-    float2 y[NR];
+    // y = Dinv r, the same tile product
 #pragma unroll
-    for (int k = 0; k < NR; ++k) y[k] = make_float2(0.f, 0.f);
+    for (int k = 0; k < NR; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
+    stream_tile_product<NR>(sm, g, q, acc0, acc1);
+    stream_reduce_q<NR>(acc0);
+    stream_reduce_q<NR>(acc1);
+    if (q == 0) {
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const float2 d = sDi[r][q * 16 + c];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) cfma(y[k], d, sR[q * 16 + c][k]);
-    }
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      y[k].x += __shfl_xor_sync(0xffffffffu, y[k].x, 1);
-      y[k].y += __shfl_xor_sync(0xffffffffu, y[k].y, 1);
-      y[k].x += __shfl_xor_sync(0xffffffffu, y[k].x, 2);
-      y[k].y += __shfl_xor_sync(0xffffffffu, y[k].y, 2);
-    }
-    if (q == 0 && r < rows) {
-#pragma unroll
-      for (int k = 0; k < NR; ++k) X[(r0 + r) * NR + k] = y[k];
+      for (int k = 0; k < NR; ++k) {
+        if (k < nc) {
+          if (g < rows) X[(r0 + g) * ldx + k0 + k] = acc0[k];
+          if (g + 32 < rows) X[(r0 + g + 32) * ldx + k0 + k] = acc1[k];
+        }
+      }
     }
     __threadfence();
     __syncthreads();
-    if (t == 0) atomicExch(flags + ib, 1);  // publish block ib
+    if (t == 0) atomicExch(flags + ib * chunks + ch, 1);  // publish chunk ch of block ib
   }
 }
 
 }  // namespace
 
-size_t trsv_stream_scratch_ints(int64_t n) { return size_t(2 * ((n + kTB - 1) / kTB) + 64); }
+// chunk width: the exact width for 1-8 right-hand sides, 16 above
+static int trsv_stream_width(int64_t nrhs) { return nrhs <= 8 ? int(nrhs) : 16; }
+
+size_t trsv_stream_scratch_ints(int64_t n, int64_t nrhs) {
+  const int64_t w = trsv_stream_width(std::max<int64_t>(nrhs, 1));
+  return size_t(((n + kTB - 1) / kTB) * ((nrhs + w - 1) / w) + 64);
+}
 
 cudaError_t tri_block_inverses_c64(const void* LU, int64_t n, int64_t ld, void* Dinv, cudaStream_t s) {
   const int64_t nblk = (n + kTB - 1) / kTB;
@@ -234,23 +295,28 @@ size_t tri_block_inverses_bytes(int64_t n) { return size_t(2 * ((n + kTB - 1) / 
 cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, const void* Dinv, void* X, int64_t nrhs, int upper,
                             int* scratch, int* status, cudaStream_t s) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  if (nrhs > 8) return cudaErrorInvalidValue;
+  if (nrhs > kTrsvStreamMaxRhs) return cudaErrorInvalidValue;
   static int nsm[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!nsm[dev]) cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
   const int64_t nblk = (n + kTB - 1) / kTB;
+  const int w = trsv_stream_width(nrhs);
+  const int chunks = int((nrhs + w - 1) / w);
   int* ticket = scratch;
   int* flags = scratch + 32;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * (32 + nblk), s);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * (32 + nblk * chunks), s);
   if (e != cudaSuccess) return e;
-  const unsigned grid = unsigned(std::min<int64_t>(nblk, int64_t(4) * std::max(nsm[dev], 1)));
+  const unsigned grid = unsigned(std::min<int64_t>(nblk * chunks, int64_t(2) * std::max(nsm[dev], 1)));
   const float2* L = static_cast<const float2*>(LU);
   const float2* D = static_cast<const float2*>(Dinv) + (upper ? nblk * kTB * kTB : 0);
   float2* x = static_cast<float2*>(X);
-#define FOSB_TS(NR) trsv_stream_kernel<NR><<<grid, 256, 0, s>>>(L, n, ld, D, x, upper, ticket, flags, status)
-  switch (nrhs) {
+  const int nr = int(nrhs);
+#define FOSB_TS(NR)                                                                                      \
+  trsv_stream_kernel<NR><<<grid, 256, sizeof(StreamSmem<NR>), s>>>(L, n, ld, D, x, nrhs, nr, chunks, upper, ticket, \
+                                                                   flags, status)
+  switch (w) {
     case 1: FOSB_TS(1); break;
     case 2: FOSB_TS(2); break;
     case 3: FOSB_TS(3); break;
@@ -258,7 +324,8 @@ cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, const void* D
     case 5: FOSB_TS(5); break;
     case 6: FOSB_TS(6); break;
     case 7: FOSB_TS(7); break;
-    default: FOSB_TS(8); break;
+    case 8: FOSB_TS(8); break;
+    default: FOSB_TS(16); break;
   }
 #undef FOSB_TS
   return launched();
