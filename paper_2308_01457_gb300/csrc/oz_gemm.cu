@@ -319,7 +319,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const int64_t k0 = c * OZ_KCH, k1 = std::min<int64_t>(KC, k0 + OZ_KCH);
-          uint32_t started = 0;  // accumulators (order, part) written in this chunk
           for (int64_t kc = k0; kc < k1; ++kc, ++it) {
             const int st = int(it % OZ_STAGES);
             const int64_t use = it / OZ_STAGES;
@@ -328,19 +327,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // descriptors of the stage's first A and B tiles; a tile at byte offset X adds
+            // X >> 4 to the address field (shared addresses stay below 2^18, no carry)
             const uint32_t a0 = smem_u32(smem + st * OZ_STAGE), b0 = a0 + OZ_NT * OZ_ATILE;
+            const uint64_t da = oz_desc(a0), db = oz_desc(b0);
+            // the first product into an order's accumulator in a chunk overwrites it
+            const uint32_t first = kc == k0 ? 0u : 1u;
+#pragma unroll
             for (int s = 0; s < OZ_ND; ++s) {
-              const uint64_t ar = oz_desc(a0 + (s * 2 + 0) * OZ_ATILE), ai = oz_desc(a0 + (s * 2 + 1) * OZ_ATILE);
-              for (int t = 0; s + t < OZ_ND; ++t) {
-                const int g = s + t;  // order 0..6
-                const uint64_t br = oz_desc(b0 + (t * 2 + 0) * OZ_BTILE), bi = oz_desc(b0 + (t * 2 + 1) * OZ_BTILE);
+              const uint64_t ar = da + uint64_t((s * 2 + 0) * (OZ_ATILE >> 4));
+              const uint64_t ai = da + uint64_t((s * 2 + 1) * (OZ_ATILE >> 4));
+#pragma unroll
+              for (int t = 0; t < OZ_ND - s; ++t) {
+                const int g = s + t;  // order 0..6; s == 0 is the first pair of order g
+                const uint64_t br = db + uint64_t((t * 2 + 0) * (OZ_BTILE >> 4));
+                const uint64_t bi = db + uint64_t((t * 2 + 1) * (OZ_BTILE >> 4));
                 const uint32_t dre = tmem + uint32_t(g * 2 + 0) * OZ_TN, dim = tmem + uint32_t(g * 2 + 1) * OZ_TN;
-                const uint32_t mre = 1u << (g * 2), mim = 1u << (g * 2 + 1);
-                oz_mma(dre, ar, br, id, (started & mre) ? 1u : 0u);
-                started |= mre;
+                oz_mma(dre, ar, br, id, s == 0 ? first : 1u);
                 oz_mma(dre, ai, bi, idn, 1u);
-                oz_mma(dim, ar, bi, id, (started & mim) ? 1u : 0u);
-                started |= mim;
+                oz_mma(dim, ar, bi, id, s == 0 ? first : 1u);
                 oz_mma(dim, ai, br, id, 1u);
               }
             }
@@ -383,28 +388,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll 1
         for (int g = 0; g < OZ_ND; ++g) {
-          uint32_t v[16];
+          // both parts of order g in flight together, one wait
+          uint32_t v[16], w[16];
           oz_ld16(tmem + (uint32_t(lane_base) << 16) + uint32_t(g * 2 + 0) * OZ_TN + c0, v);
+          oz_ld16(tmem + (uint32_t(lane_base) << 16) + uint32_t(g * 2 + 1) * OZ_TN + c0, w);
           asm volatile("tcgen05.wait::ld.sync.aligned;");
           if (g <= 3) {
             const int sh = 24 - 8 * g;
 #pragma unroll
-            for (int j = 0; j < OZ_HN; ++j) ar_[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+            for (int j = 0; j < OZ_HN; ++j) {
+              ar_[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+              ai_[j] += (long long)__float2int_rn(__uint_as_float(w[j])) << sh;
+            }
           } else {
             const float sc = __int_as_float((127 + 24 - 8 * g) << 23);  // 2^{24-8g}
 #pragma unroll
-            for (int j = 0; j < OZ_HN; ++j) tr[j] = fmaf(__uint_as_float(v[j]), sc, tr[j]);
-          }
-          oz_ld16(tmem + (uint32_t(lane_base) << 16) + uint32_t(g * 2 + 1) * OZ_TN + c0, v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-          if (g <= 3) {
-            const int sh = 24 - 8 * g;
-#pragma unroll
-            for (int j = 0; j < OZ_HN; ++j) ai_[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
-          } else {
-            const float sc = __int_as_float((127 + 24 - 8 * g) << 23);
-#pragma unroll
-            for (int j = 0; j < OZ_HN; ++j) ti[j] = fmaf(__uint_as_float(v[j]), sc, ti[j]);
+            for (int j = 0; j < OZ_HN; ++j) {
+              tr[j] = fmaf(__uint_as_float(v[j]), sc, tr[j]);
+              ti[j] = fmaf(__uint_as_float(w[j]), sc, ti[j]);
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
