@@ -19,7 +19,10 @@
 // the pre-tiled digit tiles of a 16-wide k step (14 A tiles of 4 KB, 14 B tiles of 1 KB)
 // into a 3-stage shared ring with bulk copies; warp 1 lane 0 issues 112 MMAs per step
 // (tcgen05.mma kind::f16, bf16, M = 128, N = 32, K = 16; the minus of Im Z Im X via the
-// negate-A bit) into the 14 order accumulators; warps 2-9 read the accumulators after every
+// negate-B bit; the MMAs that share an A tile and an instruction descriptor run back to
+// back and keep it in the A collector, so an A tile is read from shared memory once or
+// twice per step) into the 14 order
+// accumulators; warps 2-9 read the accumulators after every
 // 64 values of k and hold the sums (two warps per TMEM lane group, 16 columns each).  All
 // waits are bounded.
 #include <cuda_bf16.h>
@@ -62,16 +65,38 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
          (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
 }
 // kind::f16 instruction descriptor: D f32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
-// K-major A and B, N >> 3 at bits 17-22, M >> 4 at bits 24-28, optional negate-A (bit 13)
-__host__ __device__ constexpr uint32_t oz_idesc(bool neg_a) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (neg_a ? (1u << 13) : 0u) | (uint32_t(OZ_TN >> 3) << 17) |
+// K-major A and B, N >> 3 at bits 17-22, M >> 4 at bits 24-28, optional negate-B (bit 14)
+__host__ __device__ constexpr uint32_t oz_idesc(bool neg_b) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (neg_b ? (1u << 14) : 0u) | (uint32_t(OZ_TN >> 3) << 17) |
          (uint32_t(OZ_TM >> 4) << 24);
 }
-__device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+// One MMA; CU says what the A collector does: 0 = fill (read A, keep it), 1 = use the kept A,
+// 2 = use it for the last time.  Consecutive MMAs on the same A tile read it from shared
+// memory once.
+__device__ __forceinline__ void oz_mma_once(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+template <int CU>
+__device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if constexpr (CU == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else if constexpr (CU == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ bool oz_wait(uint32_t mbar, uint32_t parity) {
   for (long long spins = 0; spins < kOzSpinLimit; ++spins) {
@@ -333,20 +358,40 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint64_t da = oz_desc(a0), db = oz_desc(b0);
             // the first product into an order's accumulator in a chunk overwrites it
             const uint32_t first = kc == k0 ? 0u : 1u;
+            // Each A tile meets its B digits t = 0 .. 6 - s in consecutive MMAs that keep it in
+            // the A collector, so it is read from shared memory once per group.  A group must
+            // keep one instruction descriptor, so digit s of Re Z is one group (Re and Im of
+            // every order), digit s of Im Z two: -Im Z Im X into Re (negate-B), Im Z Re X into Im.
 #pragma unroll
             for (int s = 0; s < OZ_ND; ++s) {
               const uint64_t ar = da + uint64_t((s * 2 + 0) * (OZ_ATILE >> 4));
               const uint64_t ai = da + uint64_t((s * 2 + 1) * (OZ_ATILE >> 4));
+              const uint32_t acc = s == 0 ? first : 1u;  // s == 0 holds the first pair of each order
+              const int T = OZ_ND - s;  // B digits met by this A digit (a constant once unrolled)
 #pragma unroll
-              for (int t = 0; t < OZ_ND - s; ++t) {
-                const int g = s + t;  // order 0..6; s == 0 is the first pair of order g
+              for (int t = 0; t < T; ++t) {
+                const int g = s + t;
                 const uint64_t br = db + uint64_t((t * 2 + 0) * (OZ_BTILE >> 4));
                 const uint64_t bi = db + uint64_t((t * 2 + 1) * (OZ_BTILE >> 4));
                 const uint32_t dre = tmem + uint32_t(g * 2 + 0) * OZ_TN, dim = tmem + uint32_t(g * 2 + 1) * OZ_TN;
-                oz_mma(dre, ar, br, id, s == 0 ? first : 1u);
-                oz_mma(dre, ai, bi, idn, 1u);
-                oz_mma(dim, ar, bi, id, s == 0 ? first : 1u);
-                oz_mma(dim, ai, br, id, 1u);
+                if (t == 0) oz_mma<0>(dre, ar, br, id, acc);
+                else oz_mma<1>(dre, ar, br, id, acc);
+                if (t == T - 1) oz_mma<2>(dim, ar, bi, id, acc);
+                else oz_mma<1>(dim, ar, bi, id, acc);
+              }
+#pragma unroll
+              for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                  const int g = s + t;
+                  const uint64_t b = db + uint64_t((t * 2 + (half == 0 ? 1 : 0)) * (OZ_BTILE >> 4));
+                  const uint32_t d = tmem + uint32_t(g * 2 + half) * OZ_TN;
+                  const uint32_t idd = half == 0 ? idn : id;
+                  if (T == 1) oz_mma_once(d, ai, b, idd, 1u);
+                  else if (t == 0) oz_mma<0>(d, ai, b, idd, 1u);
+                  else if (t == T - 1) oz_mma<2>(d, ai, b, idd, 1u);
+                  else oz_mma<1>(d, ai, b, idd, 1u);
+                }
               }
             }
             oz_commit(smem_u32(&bar_empty[st]));
