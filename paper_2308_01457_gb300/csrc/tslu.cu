@@ -15,7 +15,12 @@
 // The panel stays untouched in global memory until step 3, so every level reads original
 // rows.  Launches are stream-ordered; there is no inter-CTA wait anywhere.
 //
-// Within a CTA each thread owns one row with its jb entries in registers.  Rows are never
+// Within a CTA the candidate rows sit in shared memory, one per thread, and are factored
+// by blocked partial pivoting in blocks of 8 columns: per step a warp argmax (one reduce
+// and one ballot), one barrier, and the elimination of that column inside the block; per
+// block the trailing columns of its pivot rows by forward substitution with the block's
+// unit lower factor, then one rank-8 update of every remaining row.  This is the same
+// factorisation, with the same pivots, as unblocked partial pivoting.  Rows are never
 // moved: a row that has served as pivot is marked used, keeps its (L, U) entries and is
 // skipped by later updates, so at the end the row chosen at step j holds row j of L \ U.
 #include <cuda_runtime.h>
@@ -33,28 +38,21 @@ constexpr int kTsluRows = 256;  // rows per CTA (one per thread)
 constexpr int kTsluCols = 64;   // panel width handled (jb <= 64)
 constexpr int kTsluFanIn = kTsluRows / kTsluCols;
 
-__device__ __forceinline__ unsigned long long tslu_key(float2 v, int row) {
-  // |Re| + |Im| in the upper half (float bits order like the values), ~row below: the
-  // largest key is the largest magnitude, ties going to the lowest row
-  const unsigned hi = __float_as_uint(fabsf(v.x) + fabsf(v.y));
-  return (static_cast<unsigned long long>(hi) << 32) | (0xFFFFFFFFu - static_cast<unsigned>(row));
-}
-
-__device__ __forceinline__ unsigned long long tslu_warp_max(unsigned long long k) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, off);
-    k = o > k ? o : k;
-  }
-  return k;
-}
-
 __device__ __forceinline__ float2 cinv(float2 v) {
   const float den = v.x * v.x + v.y * v.y;
   return den > 0.f ? make_float2(v.x / den, -v.y / den) : make_float2(0.f, 0.f);
 }
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+constexpr int kTsluLd = kTsluCols + 2;  // row pitch in complex values (16-byte aligned rows)
+constexpr int kTsluBlk = 8;              // columns per block of the blocked factorisation
+constexpr size_t kTsluSmem = size_t(kTsluRows) * kTsluLd * sizeof(float2);
+
+__device__ __forceinline__ void cfms(float2& a, float2 l, float2 u) {  // a -= l u
+  a.x -= l.x * u.x - l.y * u.y;
+  a.y -= l.x * u.y + l.y * u.x;
 }
 
 // Leaf mode (in_idx == nullptr): CTA b factors panel rows [b * 256, min(m, (b + 1) * 256)).
@@ -67,12 +65,13 @@ __global__ void __launch_bounds__(kTsluRows, 1)
     tslu_gepp_kernel(const float2* __restrict__ A, int64_t lda, int64_t m, int jb, const int* __restrict__ in_idx,
                      const int* __restrict__ in_cnt, int groups_in, int* __restrict__ out_idx, int* __restrict__ out_cnt,
                      float2* __restrict__ top, int* __restrict__ sel) {
+  extern __shared__ float4 tslu_raw[];
+  float2* sA = reinterpret_cast<float2*>(tslu_raw);  // [kTsluRows][kTsluLd]
   __shared__ int s_rows[kTsluRows];
-  __shared__ unsigned long long s_kmax[2];
+  __shared__ unsigned long long s_wk[kTsluRows / 32];
+  __shared__ int s_piv[kTsluBlk];
   __shared__ int s_nr;
-  __shared__ __align__(16) float2 s_u[kTsluCols];
-  __shared__ float2 s_inv;
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool root = gridDim.x == 1;
   // rows of this CTA (panel-row indices)
   if (t == 0) {
@@ -90,73 +89,128 @@ __global__ void __launch_bounds__(kTsluRows, 1)
   __syncthreads();
   const int nr = s_nr;
   const int steps = min(nr, jb);
-  const int myrow = t < nr ? s_rows[t] : -1;
-  float2 w[kTsluCols];
+  // rows into shared memory, a warp per row (256 contiguous bytes per load instruction),
+  // eight rows' loads in flight before any store; zero past jb and for missing rows
+  constexpr int kWarps = kTsluRows / 32, kBatch = 8;
+  for (int r0 = warp; r0 < kTsluRows; r0 += kWarps * kBatch) {
+    float2 v[kBatch][2];
 #pragma unroll
-  for (int c = 0; c < kTsluCols; ++c) w[c] = make_float2(0.f, 0.f);
-  if (myrow >= 0) {
-    const float2* src = A + int64_t(myrow) * lda;
+    for (int b = 0; b < kBatch; ++b) {
+      const int r = r0 + b * kWarps;
+      const float2* src = A + int64_t(r < nr ? s_rows[r] : 0) * lda;
+      v[b][0] = (r < nr && lane < jb) ? __ldg(src + lane) : make_float2(0.f, 0.f);
+      v[b][1] = (r < nr && lane + 32 < jb) ? __ldg(src + lane + 32) : make_float2(0.f, 0.f);
+    }
 #pragma unroll
-    for (int c = 0; c < kTsluCols; ++c)
-      if (c < jb) w[c] = __ldg(src + c);
+    for (int b = 0; b < kBatch; ++b) {
+      float2* dst = sA + (r0 + b * kWarps) * kTsluLd;
+      dst[lane] = v[b][0];
+      dst[lane + 32] = v[b][1];
+      if (lane < kTsluLd - kTsluCols) dst[kTsluCols + lane] = make_float2(0.f, 0.f);
+    }
   }
-  // Rotating layout: before step j, w[0] holds column j and w[1 .. 63 - j] the later columns;
-  // the multipliers found so far follow.  A step consumes w[0], shifts the live columns
-  // left (subtracting l times the pivot row) and appends the new multiplier at the end; a
-  // row that is already a pivot row (or any row once the panel's columns run out) only
-  // rotates.  Every step is the same code with static register indices, so the loop stays
-  // rolled.  After step 31 every row's live columns fit in w[0..31]: steps 32..63 rotate
-  // only that half, and the final layout is w[(c + 32) % 64] = column c.
-  bool used = myrow < 0;
-  int order = -1;
-  if (t < 2) s_kmax[t] = 0ull;
   __syncthreads();
-  auto step = [&](int j, auto width_tag) {
-    constexpr int W = decltype(width_tag)::value;  // rotated width (64 or 32)
-    const bool piv_step = j < steps;
-    if (piv_step) {
-      unsigned long long k = used ? 0ull : tslu_key(w[0], t);
-      k = tslu_warp_max(k);
-      if (lane == 0 && k) atomicMax(&s_kmax[j & 1], k);
+  bool used = t >= nr;
+  int order = -1;
+  float2* my = sA + t * kTsluLd;
+  for (int cb = 0; cb < steps; cb += kTsluBlk) {
+    const int ce = min(cb + kTsluBlk, steps);  // pivot steps of this block
+    const int cbe = min(cb + kTsluBlk, jb);    // columns of this block
+    for (int j = cb; j < ce; ++j) {
+      // pivot: the largest |Re| + |Im| in column j among unused rows, ties to the lowest row
+      unsigned key = 0;
+      if (!used) {
+        const float2 v = my[j];
+        key = __float_as_uint(fabsf(v.x) + fabsf(v.y));
+      }
+      const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+      const unsigned bal = __ballot_sync(0xffffffffu, !used && key == mk);
+      if (lane == 0)
+        s_wk[warp] = bal ? (static_cast<unsigned long long>(mk) << 32) |
+                               (0xFFFFFFFFu - unsigned(warp * 32 + __ffs(bal) - 1))
+                         : 0ull;
       __syncthreads();
-      const unsigned long long kk = s_kmax[j & 1];
-      const int p = int(0xFFFFFFFFu - unsigned(kk & 0xFFFFFFFFull));
-      if (t == 0) s_kmax[(j + 1) & 1] = 0ull;  // every thread has finished reading it
+      unsigned long long best = s_wk[0];
+#pragma unroll
+      for (int w = 1; w < kTsluRows / 32; ++w) best = s_wk[w] > best ? s_wk[w] : best;
+      const int p = int(0xFFFFFFFFu - unsigned(best & 0xFFFFFFFFull));  // an unused row exists: j < nr
       if (t == p) {
         used = true;
         order = j;
-        // the pivot row, pre-shifted by one (s_u[c] pairs with w[c + 1]), zero past its live part
-#pragma unroll
-        for (int c = 0; c < W - 1; ++c) s_u[c] = c <= 62 - j ? w[c + 1] : make_float2(0.f, 0.f);
-        s_inv = cinv(w[0]);
       }
-      __syncthreads();
-    }
-    const bool live = piv_step && !used;
-    const float2 l = live ? cmulf(w[0], s_inv) : make_float2(0.f, 0.f);
-    const float2 last = live ? l : w[0];
-    const float4* u4 = reinterpret_cast<const float4*>(s_u);
+      if (t == 0) s_piv[j - cb] = p;
+      if (!used) {  // eliminate column j inside the block (all loads before the stores)
+        const float2* pr = sA + p * kTsluLd;
+        float2 pu[kTsluBlk], mv[kTsluBlk];
 #pragma unroll
-    for (int c = 0; c < W - 1; c += 2) {
-      const float4 u = u4[c >> 1];  // pivot entries paired with w[c + 1], w[c + 2]
-      w[c].x = w[c + 1].x - (l.x * u.x - l.y * u.y);
-      w[c].y = w[c + 1].y - (l.x * u.y + l.y * u.x);
-      if (c + 1 < W - 1) {
-        w[c + 1].x = w[c + 2].x - (l.x * u.z - l.y * u.w);
-        w[c + 1].y = w[c + 2].y - (l.x * u.w + l.y * u.z);
+        for (int q = 0; q < kTsluBlk; ++q) {
+          const int k = cb + q;
+          if (k >= j && k < cbe) {
+            pu[q] = pr[k];
+            mv[q] = my[k];
+          }
+        }
+        float2 l = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kTsluBlk; ++q)
+          if (cb + q == j) l = cmulf(mv[q], cinv(pu[q]));
+#pragma unroll
+        for (int q = 0; q < kTsluBlk; ++q) {
+          const int k = cb + q;
+          if (k == j) my[k] = l;
+          if (k > j && k < cbe) {
+            cfms(mv[q], l, pu[q]);
+            my[k] = mv[q];
+          }
+        }
+      }
+      __syncthreads();  // column j + 1 is up to date; s_wk may be rewritten
+    }
+    if (cbe >= jb) continue;
+    const int npiv = ce - cb;
+    // trailing columns of the block's pivot rows: U12 = L11^{-1} A12 (L11 unit lower, the
+    // multipliers the pivot rows received inside the block), one thread per column
+    for (int k = cbe + t; k < jb; k += blockDim.x) {
+      for (int i = 0; i < npiv; ++i) {
+        float2* ui = sA + s_piv[i] * kTsluLd;
+        float2 u = ui[k];
+        for (int q = 0; q < i; ++q) cfms(u, ui[cb + q], sA[s_piv[q] * kTsluLd + k]);
+        ui[k] = u;
       }
     }
-    w[W - 1] = last;
-    if (piv_step) __syncthreads();  // s_u is rewritten by the next pivot
-  };
-  for (int j = 0; j < kTsluCols / 2; ++j) step(j, std::integral_constant<int, kTsluCols>{});
-  for (int j = kTsluCols / 2; j < kTsluCols; ++j) step(j, std::integral_constant<int, kTsluCols / 2>{});
+    __syncthreads();
+    // rank-npiv update of the rows not chosen yet, two columns per 16-byte access
+    if (!used) {
+      float2 l[kTsluBlk];
+      const float2* pv[kTsluBlk];
+#pragma unroll
+      for (int q = 0; q < kTsluBlk; ++q) {
+        l[q] = q < npiv ? my[cb + q] : make_float2(0.f, 0.f);
+        pv[q] = sA + s_piv[q < npiv ? q : 0] * kTsluLd;
+      }
+      for (int k = cbe; k < jb; k += 2) {
+        float4 a = *reinterpret_cast<const float4*>(my + k);
+        float4 u[kTsluBlk];
+#pragma unroll
+        for (int q = 0; q < kTsluBlk; ++q)
+          u[q] = q < npiv ? *reinterpret_cast<const float4*>(pv[q] + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kTsluBlk; ++q) {
+          a.x -= l[q].x * u[q].x - l[q].y * u[q].y;
+          a.y -= l[q].x * u[q].y + l[q].y * u[q].x;
+          a.z -= l[q].x * u[q].z - l[q].y * u[q].w;
+          a.w -= l[q].x * u[q].w + l[q].y * u[q].z;
+        }
+        *reinterpret_cast<float4*>(my + k) = a;
+      }
+    }
+    __syncthreads();
+  }
   if (order >= 0) {
-    out_idx[blockIdx.x * kTsluCols + order] = myrow;
+    out_idx[blockIdx.x * kTsluCols + order] = s_rows[t];
     if (root) {
-      sel[order] = myrow;
-#pragma unroll
-      for (int c = 0; c < kTsluCols; ++c) top[order * kTsluCols + c] = w[(c + kTsluCols / 2) % kTsluCols];
+      sel[order] = s_rows[t];
+      for (int c = 0; c < kTsluCols; ++c) top[order * kTsluCols + c] = my[c];
     }
   }
   if (t == 0) out_cnt[blockIdx.x] = steps;
@@ -300,12 +354,22 @@ cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, 
   int* sel = cnt1 + leaves_max;
   int groups = int((m + kTsluRows - 1) / kTsluRows);
   if (groups > leaves_max) return cudaErrorInvalidValue;
-  tslu_gepp_kernel<<<groups, kTsluRows, 0, s>>>(A, lda, m, jb, nullptr, nullptr, 0, idx0, cnt0, top, sel);
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(tslu_gepp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(kTsluSmem));
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  tslu_gepp_kernel<<<groups, kTsluRows, kTsluSmem, s>>>(A, lda, m, jb, nullptr, nullptr, 0, idx0, cnt0, top, sel);
   uint64_t nl = 1;
   int *in_i = idx0, *in_c = cnt0, *out_i = idx1, *out_c = cnt1;
   while (groups > 1) {
     const int next = (groups + kTsluFanIn - 1) / kTsluFanIn;
-    tslu_gepp_kernel<<<next, kTsluRows, 0, s>>>(A, lda, m, jb, in_i, in_c, groups, out_i, out_c, top, sel);
+    tslu_gepp_kernel<<<next, kTsluRows, kTsluSmem, s>>>(A, lda, m, jb, in_i, in_c, groups, out_i, out_c, top, sel);
     ++nl;
     groups = next;
     int* ti = in_i; in_i = out_i; out_i = ti;
@@ -315,9 +379,6 @@ cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, 
   ++nl;
   if (m > jb) {
     static int nsm[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!nsm[dev]) cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
     const unsigned g = std::min<unsigned>(cdivu(m - jb, 8), unsigned(6 * std::max(nsm[dev], 1)));
     tslu_lsolve_kernel<<<g, 256, 0, s>>>(A, lda, m, jb);
