@@ -381,31 +381,30 @@ def cpu_baseline(W, budget_s: float = 20.0):
     O.build()
     cores = O.n_threads()
     t_begin = time.perf_counter()
-    # assembly sample: the largest level that fits the budget (start small)
+    def mesh(lvl):
+        return O.from_synth(S.icosphere(lvl) if W["mesh"] == "sphere" else S.torus(10 * 2 ** (lvl - 1), 4 * 2 ** (lvl - 1)))
+
+    # assembly sample: successively larger levels while the next one, predicted from the
+    # rate just measured, fits in about half of the budget
     asm_rate, asm_lvl = None, None
-    for lvl in (2, 3):
-        m = O.from_synth(S.icosphere(lvl) if W["mesh"] == "sphere" else S.torus(10 * 2 ** (lvl - 1), 4 * 2 ** (lvl - 1)))
+    for lvl in (2, 3, 4):
+        m = mesh(lvl)
+        if asm_rate is not None and (time.perf_counter() - t_begin) + m.n_edges**2 / asm_rate > 0.5 * budget_s:
+            break
         t0 = time.perf_counter()
         O.assemble_z(m, W["k"])
-        dt = time.perf_counter() - t0
-        asm_rate, asm_lvl = m.n_edges**2 / dt, lvl
-        if time.perf_counter() - t_begin > budget_s / 3:
-            break
-    # LU sample
-    n_lu = 1920
+        asm_rate, asm_lvl = m.n_edges**2 / (time.perf_counter() - t0), lvl
+    # LU sample: the same, up to N = 7680, within the whole budget
     rng = np.random.default_rng(0)
-    A = rng.standard_normal((n_lu, n_lu)) + 1j * rng.standard_normal((n_lu, n_lu))
-    b = rng.standard_normal((n_lu, 1)) + 0j
-    t0 = time.perf_counter()
-    np.linalg.solve(A, b)
-    lu_rate = (8.0 / 3.0) * n_lu**3 / (time.perf_counter() - t0)
-    if time.perf_counter() - t_begin < budget_s / 2:
-        n_lu = 3840
-        A = rng.standard_normal((n_lu, n_lu)) + 1j * rng.standard_normal((n_lu, n_lu))
-        b = rng.standard_normal((n_lu, 1)) + 0j
+    lu_rate, n_lu = None, None
+    for n in (1920, 3840, 7680):
+        if lu_rate is not None and (time.perf_counter() - t_begin) + (8.0 / 3.0) * n**3 / lu_rate > budget_s:
+            break
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        b = rng.standard_normal((n, 1)) + 0j
         t0 = time.perf_counter()
         np.linalg.solve(A, b)
-        lu_rate = (8.0 / 3.0) * n_lu**3 / (time.perf_counter() - t0)
+        lu_rate, n_lu = (8.0 / 3.0) * n**3 / (time.perf_counter() - t0), n
     N = {l: _n_edges(W, l) for l in W["levels"]}
     t_asm = sum(N[l] ** 2 / asm_rate for l in N)
     t_lu = lambda n: (8.0 / 3.0) * n**3 / lu_rate  # noqa: E731
