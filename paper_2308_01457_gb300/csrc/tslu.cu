@@ -40,7 +40,9 @@ constexpr int kTsluFanIn = kTsluRows / kTsluCols;
 
 __device__ __forceinline__ float2 cinv(float2 v) {
   const float den = v.x * v.x + v.y * v.y;
-  return den > 0.f ? make_float2(v.x / den, -v.y / den) : make_float2(0.f, 0.f);
+  if (!(den > 0.f)) return make_float2(0.f, 0.f);
+  const float r = 1.f / den;
+  return make_float2(v.x * r, -v.y * r);
 }
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -116,7 +118,11 @@ __global__ void __launch_bounds__(kTsluRows, 1)
   for (int cb = 0; cb < steps; cb += kTsluBlk) {
     const int ce = min(cb + kTsluBlk, steps);  // pivot steps of this block
     const int cbe = min(cb + kTsluBlk, jb);    // columns of this block
-    for (int j = cb; j < ce; ++j) {
+    // the eight steps of the block, each compiled for its position JJ inside the block
+    auto step = [&](auto jj_tag) {
+      constexpr int JJ = decltype(jj_tag)::value;
+      const int j = cb + JJ;
+      if (j >= ce) return;  // the same for every thread
       // pivot: the largest |Re| + |Im| in column j among unused rows, ties to the lowest row
       unsigned key = 0;
       if (!used) {
@@ -138,34 +144,38 @@ __global__ void __launch_bounds__(kTsluRows, 1)
         used = true;
         order = j;
       }
-      if (t == 0) s_piv[j - cb] = p;
+      if (t == 0) s_piv[JJ] = p;
       if (!used) {  // eliminate column j inside the block (all loads before the stores)
+        constexpr int W = kTsluBlk - JJ;
         const float2* pr = sA + p * kTsluLd;
-        float2 pu[kTsluBlk], mv[kTsluBlk];
+        float2 pu[W], mv[W];
 #pragma unroll
-        for (int q = 0; q < kTsluBlk; ++q) {
-          const int k = cb + q;
-          if (k >= j && k < cbe) {
-            pu[q] = pr[k];
-            mv[q] = my[k];
+        for (int q = 0; q < W; ++q) {
+          if (j + q < cbe) {
+            pu[q] = pr[j + q];
+            mv[q] = my[j + q];
           }
         }
-        float2 l = make_float2(0.f, 0.f);
+        const float2 l = cmulf(mv[0], cinv(pu[0]));
+        my[j] = l;
 #pragma unroll
-        for (int q = 0; q < kTsluBlk; ++q)
-          if (cb + q == j) l = cmulf(mv[q], cinv(pu[q]));
-#pragma unroll
-        for (int q = 0; q < kTsluBlk; ++q) {
-          const int k = cb + q;
-          if (k == j) my[k] = l;
-          if (k > j && k < cbe) {
+        for (int q = 1; q < W; ++q) {
+          if (j + q < cbe) {
             cfms(mv[q], l, pu[q]);
-            my[k] = mv[q];
+            my[j + q] = mv[q];
           }
         }
       }
       __syncthreads();  // column j + 1 is up to date; s_wk may be rewritten
-    }
+    };
+    step(std::integral_constant<int, 0>{});
+    step(std::integral_constant<int, 1>{});
+    step(std::integral_constant<int, 2>{});
+    step(std::integral_constant<int, 3>{});
+    step(std::integral_constant<int, 4>{});
+    step(std::integral_constant<int, 5>{});
+    step(std::integral_constant<int, 6>{});
+    step(std::integral_constant<int, 7>{});
     if (cbe >= jb) continue;
     const int npiv = ce - cb;
     // trailing columns of the block's pivot rows: U12 = L11^{-1} A12 (L11 unit lower, the
