@@ -172,8 +172,13 @@ fosb_status fosb_assemble_efie(fosb_mesh mesh, double k, const fosb_quad_opts* o
  *          read, not modified.  For FOSB_MIXED the handle keeps a NON-owning reference
  *          to Z for the FP64 residuals: Z must stay alive and unchanged until
  *          fosb_lu_destroy.
- *   out  : receives a handle owning the factors and pivots (device memory).
- * Synchronises `stream` at the end (the pivot search reports FOSB_ERR_SINGULAR). */
+ *   out  : receives a handle owning the factors and pivots (device memory).  A FOSB_MIXED
+ *          handle also owns two residual copies of Z: a float-float split (16 n^2 bytes)
+ *          and, for n >= 256, exact bf16 digit tiles (28 n^2 bytes) for the FP64-class
+ *          tensor-core residuals of solves with 5 or more right-hand sides; and the
+ *          inverses of its 64 x 64 diagonal blocks for the streaming triangular sweeps.
+ * Synchronises `stream` at the end (the pivot search reports FOSB_ERR_SINGULAR).
+ * Errors: FOSB_ERR_OOM when device memory runs out (nothing is leaked). */
 fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu* out, void* stream);
 
 /* ---- A6: solves with iterative refinement -----------------------------------------
@@ -182,7 +187,11 @@ fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu
  *          complex64 for FP32.  X may alias B.
  *   ropt : refinement options (MIXED only; NULL -> defaults); stats may be NULL.
  * MIXED: x0 from the complex64 factors, then r = b - Z x in FP64, x += LU^{-1} r until
- * the backward error is below tol; synchronises `stream` once per step.
+ * the backward error is below tol; synchronises `stream` once per step.  The residual
+ * product is float-float for 1-4 right-hand sides and exact digit splitting on the bf16
+ * tensor cores for more (n >= 256); both are accurate to a few units of 2^-52 of
+ * |b| + |Z||x|.  Triangular sweeps of complex64 factors with up to 1024 right-hand sides
+ * run as one persistent kernel per sweep.
  * Errors: FOSB_ERR_NOT_CONVERGED (best iterate written). */
 fosb_status fosb_solve(fosb_lu lu, char op, const void* B, int64_t nrhs, int64_t ldb, void* X, int64_t ldx,
                        const fosb_refine_opts* ropt, fosb_solve_stats* stats, void* stream);
