@@ -149,11 +149,6 @@ __global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst
     for (int b = 0; b < 3; ++b) touch |= v1[a] == v2[b];
   if (touch) return;
   const float* F = m.tri_ff;
-  ff yq[6][3];
-#pragma unroll
-  for (int q = 0; q < 6; ++q)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) yq[q][c] = ldff(F, nt, (q * 3 + c) * 2, t2);
   ff D[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) D[c] = ff_add(ldff(F, nt, 36 + 2 * c, t1), ff_neg(ldff(F, nt, 36 + 2 * c, t2)));
@@ -170,11 +165,13 @@ __global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst
     CFF A[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) A[b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
+    // two point pairs per iteration: enough independent work per warp, a third of the code
+    // of a full unroll (instruction fetch bounded the fully unrolled loop)
+#pragma unroll 2
     for (int q = 0; q < 6; ++q) {
-      ff dx = ff_add_fast(E[0], ff_neg(yq[q][0]));
-      ff dy = ff_add_fast(E[1], ff_neg(yq[q][1]));
-      ff dz = ff_add_fast(E[2], ff_neg(yq[q][2]));
+      ff dx = ff_add_fast(E[0], ff_neg(ldff(F, nt, (q * 3 + 0) * 2, t2)));
+      ff dy = ff_add_fast(E[1], ff_neg(ldff(F, nt, (q * 3 + 1) * 2, t2)));
+      ff dz = ff_add_fast(E[2], ff_neg(ldff(F, nt, (q * 3 + 2) * 2, t2)));
       ff r2 = ff_add_fast(ff_add_fast(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
       const float y0 = rsqrtf(r2.h);
       const float s0 = r2.h * y0;
