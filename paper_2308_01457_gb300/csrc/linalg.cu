@@ -3,12 +3,17 @@
 //   * gemm: C = alpha op(A) op(B) + beta C, complex128 or complex64.  A 64 x 64 tiled SIMT
 //     kernel for wide products and a row-per-warp kernel for skinny products
 //     (<= 8 right-hand sides), which streams A once at HBM speed (IR residuals).
-//   * getrf: blocked right-looking LU with partial pivoting.  The panel is factored by a
-//     cooperative kernel whose CTAs own row chunks and meet at a software grid barrier
-//     once per column (bounded spin: on time-out the status word is set and the kernel
-//     returns).  Row swaps, the unit-lower triangular solve of the block row and the
-//     trailing update (gemm) follow.
-//   * getrs: forward / backward substitution by diagonal-block solves plus gemm updates.
+//   * getrf: blocked right-looking LU.  complex64 factors: 128-column blocks, each factored
+//     as two 64-column tournament-pivoting panels (tslu.cu), with the tcgen05 3xTF32
+//     trailing update (tc_gemm.cu, K = 128).  complex128 factors: 64-column panels by a
+//     cooperative partial-pivoting kernel whose CTAs own row chunks and meet at a software
+//     grid barrier once per column (bounded spin: on time-out the status word is set and
+//     the kernel returns), then row swaps, the unit-lower solve of the block row and the
+//     trailing update (gemm).
+//   * getrs: complex64 factors with up to 1024 right-hand sides run one persistent
+//     streaming kernel per sweep (trsv_stream.cu); otherwise forward / backward
+//     substitution by diagonal-block solves plus gemm updates.
+//   * gemm_c128_ff: FP64-class complex128 products in float-float on the FP32 pipe.
 #include <cuda_runtime.h>
 
 #include <algorithm>
