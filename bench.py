@@ -135,6 +135,18 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(value: float, ws: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (the whole job's time per step: every replica has
+    finished its step when the slowest has).  One rank: the value itself."""
+    if ws <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_fosb(args):
     import torch
@@ -191,11 +203,7 @@ def run_fosb(args):
         F.lib().fosb_profile_read(fam.encode(), ctypes.byref(ms_c), ctypes.byref(n_c), ctypes.byref(w_c))
         fam_stats[fam] = {"ms_per_step": ms_c.value / args.steps, "launches_per_step": n_c.value / args.steps,
                           "work_per_step": w_c.value / args.steps}
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(t_start.elapsed_time(t_end) / args.steps, ws, "cuda")
 
     def avg(name):
         v = timers.get(name, [])
