@@ -1415,7 +1415,10 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
     if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, dinv, tmp, nrhs, 0, flags, status, s);
     if (e == cudaSuccess) e = trsv_stream_c64(LU, n, ldlu, dinv, tmp, nrhs, 1, flags, status, s);
     if (flags) cudaFreeAsync(flags, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+      cudaFreeAsync(tmp, s);
+      return e;
+    }
     copy_kernel<V><<<cdiv(n * nrhs, 256), 256, 0, s>>>(tmp, n, nrhs, nrhs, X, ldx);
     note_launches(2);  // gather + final copy
     cudaFreeAsync(tmp, s);
@@ -1442,7 +1445,10 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
       else
         e = gemm<T>(OP_N, OP_N, rest, nrhs, ib, -1.0, 0.0, LU + (i0 + ib) * ldlu + i0, ldlu, tmp + i0 * nrhs, nrhs,
                     1.0, tmp + (i0 + ib) * nrhs, nrhs, s);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) {
+        cudaFreeAsync(tmp, s);
+        return e;
+      }
     }
   }
   // backward: upper
@@ -1455,7 +1461,10 @@ cudaError_t getrs(const void* LUv, int64_t n, int64_t ldlu, const int32_t* perm,
         e = cgemm_update_tc(i0, nrhs, ib, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, tmp, nrhs, status, s, "trsm_update");
       else
         e = gemm<T>(OP_N, OP_N, i0, nrhs, ib, -1.0, 0.0, LU + i0, ldlu, tmp + i0 * nrhs, nrhs, 1.0, tmp, nrhs, s);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess) {
+        cudaFreeAsync(tmp, s);
+        return e;
+      }
     }
   }
   copy_kernel<V><<<cdiv(n * nrhs, 256), 256, 0, s>>>(tmp, n, nrhs, nrhs, X, ldx);
