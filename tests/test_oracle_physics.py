@@ -158,6 +158,13 @@ def test_monte_carlo_matches_first_order_covariance(oracle_mod):
     assert var_rel < 0.35, var_rel
     full_rel = np.linalg.norm(mc - cov) / np.linalg.norm(cov)
     assert full_rel < 0.4, full_rel
+    # RCS_dB of the perturbed meshes: its sample variance / t^2 against the delta method on
+    # the first-order covariance and pseudo-covariance (the paper's MC-vs-FOSB comparison)
+    pcov = A @ O.covariance(Z, B, Z, B, K, pseudo=True) @ A.T
+    pred = O.rcs_variance_db(F0.reshape(-1, 3), cov, pcov)
+    rcs = O.rcs_db((F0[None] + t * D).reshape(M, -1, 3))
+    ratio = np.var(rcs, axis=0) / t**2 / pred
+    assert np.abs(np.median(ratio) - 1) < 0.25 and np.abs(ratio - 1).max() < 0.6, ratio
 
 
 # ---------------------------------------------------------------- combination technique
