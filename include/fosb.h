@@ -204,17 +204,21 @@ fosb_status fosb_lu_destroy(fosb_lu lu);
  * that cannot call cudaMalloc/cudaFree while they use the library (hosts whose own
  * allocator owns all device memory, or that forbid allocation after start-up because it
  * can synchronise the device), it factors the caller's matrix in place, P A = L U with
- * the same partial pivoting and kernels as fosb_factor, and allocates nothing: the panel
- * kernel's scratch lives in a 1 MiB static device array that every GPU loading the
- * library holds until the process exits.
+ * classic partial pivoting (largest |Re| + |Im|, ties to the lowest row) by a cooperative
+ * panel kernel in 64-column blocks, and allocates nothing: the panel kernel's scratch lives
+ * in a 1 MiB static device array that every GPU loading the library holds until the
+ * process exits.  For complex128 these are fosb_factor's pivots and kernels; for complex64
+ * fosb_factor uses tournament pivoting in 128-column blocks, so the pivots and factors of
+ * the two calls can differ while the solutions agree to rounding.
  *   A    : device, n x n row-major (lda >= n), complex128 (prec = FOSB_FP64) or complex64
  *          (prec = FOSB_FP32); overwritten by L (unit lower, below the diagonal) and U.
  *   ipiv : device, n int32: at step i row i was interchanged with row ipiv[i] (0-based).
- * Limits: n <= 524288 (256 panel CTAs of at most 2048 rows); larger n -> FOSB_ERR_INVALID_ARG.
+ * Limits: n <= min(SM count, 256) x 2048 (the first panel's rows over the co-resident panel
+ * CTAs, 2048 rows each): 311,296 on a 152-SM GB300; larger n -> FOSB_ERR_INVALID_ARG.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Calls share
- * the array: calls that overlap on the GPU race.  Synchronises `stream` to read the
- * status word.  Errors: FOSB_ERR_SINGULAR, FOSB_ERR_TIMEOUT, FOSB_ERR_INVALID_ARG. */
+ * with that device current.  Every call synchronises `stream` to read the status word, so
+ * no call can be made inside a stream capture.  Calls share the array: calls that overlap
+ * on the GPU race.  Errors: FOSB_ERR_SINGULAR, FOSB_ERR_TIMEOUT, FOSB_ERR_INVALID_ARG. */
 fosb_status fosb_getrf_static(void* A, int64_t n, int64_t lda, int prec, int32_t* ipiv, void* stream);
 
 /* ---- A7-A9: shape-derivative covariance of one combination-technique block --------
@@ -255,25 +259,58 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
                                   const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
                                   int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream);
 
+/* ---- A11: RCS mean and variance per direction ---------------------------------------
+ * From the moments of fosb_farfield_moments, for every observation direction d (mean far
+ * field f = F_d, 3 x 3 blocks C = Cov[F'_d] and P = E[F'_d F'_d^T] of the covariance and
+ * pseudo-covariance, Sections II-C, III and IV-B):
+ *   rcs_db[d] = 10 log10 sigma_d with sigma_d = |f|^2 / (4 pi) (convention 0: F of the expansion
+ *               E_sc ~ exp(ik|x|)/(4 pi |x|) F, eq. RCS read with it), or sigma_d = 4 pi |f|^2
+ *               (convention 1: the formula as printed; 10 log10((4 pi)^2) = 21.98 dB higher);
+ *   var_db[d] = (20/ln 10)^2 Var[Re z] / |f|^4, z = f^H F'_d, Var[Re z] = (f^H C f + Re f^H P conj f)/2
+ *               (first-order delta method; the same for both conventions);
+ *   var_f[3d + c] = C_cc: the variance of each far-field component.
+ *   F     : device, 3 n_dir complex (complex128 for FOSB_FP64/MIXED, complex64 for FOSB_FP32);
+ *           component c of direction d at F[(3d + c) * incf] (incf = ncols of a mean-mode output)
+ *   cov, pcov : device (3 n_dir) x (3 n_dir) row-major (ldc, ldp >= 3 n_dir); cov is needed by
+ *           var_db and var_f, pcov by var_db, otherwise either may be NULL
+ *   rcs_db, var_db : device n_dir float64; var_f : device 3 n_dir float64; each may be NULL
+ * Enqueued on `stream` (no synchronisation).  Errors: FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_rcs_moments(int64_t n_dir, const void* F, int64_t incf, const void* cov, int64_t ldc, const void* pcov,
+                             int64_t ldp, int prec, int convention, double* rcs_db, double* var_db, double* var_f,
+                             void* stream);
+
 /* ---- A12: monostatic RCS and its adjoint shape gradient --------------------------
  * For n plane waves E_inc_i = p_i exp(ik d_i . x) with solved currents U (u_i = Z^{-1} b_i),
  * the monostatic far field F_i = F(xh_i), xh_i = -d_i (Section II-C expansion), and
  *     sigma_i = |F_i|^2 / (4 pi)            (eq. RCS read with that expansion: RCS_dB = 10 log10 sigma).
- * With grad != NULL the call also writes grad = sum_i weights_i d sigma_i / dX (V x 3, the
- * exact derivative of the discrete sigma with respect to every vertex coordinate):
+ * With grad != NULL the call also writes grad = sum_i weights_i d q_i / dX (V x 3, the exact
+ * derivative of the discrete q_i = sigma_i, or RCS_dB_i when db = 1, with respect to every
+ * vertex coordinate):
  *     d sigma_i = (2/(4 pi)) Re[conj(F_i) . (dA_i u_i + A_i Z^{-1}(db_i - dZ u_i))],
+ *     d RCS_dB_i = 10 / (sigma_i ln 10) d sigma_i,
  * evaluated by the adjoint lambda_i = Z^{-1} A_i^T c_i (Z^T = Z) and reverse-mode kernels
  * over the same triangle pairs and quadrature points as the assembly.  The paper
  * differentiates the continuous problem (Section III); this is the discrete counterpart.
  *   lu      : factorisation of Z (FOSB_FP64 or FOSB_MIXED); needed only with grad
  *   inc     : host, n x 9 (d, Re p, Im p) as in fosb_assemble_efie
  *   U       : device, N x n complex128 (ldu >= n)
- *   weights : host, n (dL/dsigma_i); needed only with grad
- *   sigma   : host, n outputs (may be NULL);  grad : device, V x 3 float64 (overwritten) or NULL
+ *   weights : host, n (dL/dq_i); needed only with grad
+ *   db      : 0: q = sigma (m^2); 1: q = RCS_dB
+ *   sigma   : host, n outputs q_i (may be NULL);  grad : device, V x 3 float64 (overwritten) or NULL
  * Synchronises `stream`. */
 fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb_quad_opts* opts, const double* inc,
-                                int64_t n_inc, const void* U, int64_t ldu, const double* weights, double* sigma,
+                                int64_t n_inc, const void* U, int64_t ldu, const double* weights, int db, double* sigma,
                                 double* grad, void* stream);
+
+/* ---- Diagnostics: bounded device waits ---------------------------------------------
+ * Every spin-wait of the library's kernels gives up after a number of polls, sets the
+ * status word of the call to FOSB_ERR_TIMEOUT and returns, so the call reports
+ * FOSB_ERR_TIMEOUT and the context stays usable.  This sets that number for the LU panel
+ * grid barriers and the streaming triangular-sweep flags on the current device (polls <= 0
+ * restores the default 2^26, about 2 s); failure-detection tests use a tiny limit to make
+ * the waits run out.  The tensor-core kernels keep their own limits.  A factorisation whose
+ * wait ran out leaves its outputs unspecified; destroy and recreate its handle. */
+fosb_status fosb_debug_set_wait_limit(int64_t polls);
 
 #ifdef __cplusplus
 }

@@ -67,7 +67,8 @@ def lib():
         for name in ("fosb_mesh_create", "fosb_mesh_info", "fosb_mesh_edges", "fosb_mesh_destroy",
                      "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
                      "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
-                     "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read"):
+                     "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read", "fosb_rcs_moments",
+                     "fosb_debug_set_wait_limit"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -223,9 +224,9 @@ def farfield_moments(m1: Mesh, k: float, dirs, X, out, m2: Mesh | None = None, w
 
 
 def rcs_monostatic(mesh: Mesh, k: float, inc, U, lu: LU | None = None, weights=None, grad=None, n_ss: int = 5,
-                   stream=None):
-    """fosb_rcs_monostatic: sigma_i = |F(-d_i)|^2/(4 pi) (numpy, n) for solved currents U
-    (N x n); with `grad` (device V x 3 float64) also sum_i weights_i d sigma_i / dX."""
+                   db: bool = False, stream=None):
+    """fosb_rcs_monostatic: q_i = sigma_i = |F(-d_i)|^2/(4 pi), or RCS_dB_i with db=True (numpy, n),
+    for solved currents U (N x n); with `grad` (device V x 3 float64) also sum_i weights_i dq_i/dX."""
     inc_a = _np(inc, np.float64).reshape(-1, 9)
     n = inc_a.shape[0]
     sig = np.zeros(n)
@@ -234,7 +235,31 @@ def rcs_monostatic(mesh: Mesh, k: float, inc, U, lu: LU | None = None, weights=N
     _check(lib().fosb_rcs_monostatic(mesh.handle, None if lu is None else lu.handle, ctypes.c_double(k),
                                      ctypes.byref(opts), inc_a.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n),
                                      _ptr(U), ctypes.c_int64(_ld(U)),
-                                     None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                                     None if w is None else w.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(int(db)),
                                      sig.ctypes.data_as(ctypes.c_void_p), None if grad is None else _ptr(grad),
                                      _stream(stream)))
     return sig
+
+
+def rcs_moments(n_dir: int, F, cov=None, pcov=None, rcs_db=None, var_db=None, var_f=None, incf: int | None = None,
+                convention: int = 0, prec: int | None = None, stream=None):
+    """fosb_rcs_moments: per direction, RCS_dB of the mean far field F (3 n_dir complex; a
+    column of a mean-mode output), the delta-method variance of RCS_dB from the covariance
+    and pseudo-covariance blocks, and the variance of each far-field component.  Outputs are
+    device float64 tensors (rcs_db, var_db: n_dir; var_f: 3 n_dir); any may be None."""
+    prec = _prec_of(F) if prec is None else prec
+    if incf is None:
+        incf = 1 if F.dim() == 1 else _ld(F)
+    _check(lib().fosb_rcs_moments(ctypes.c_int64(n_dir), _ptr(F), ctypes.c_int64(incf),
+                                  None if cov is None else _ptr(cov), ctypes.c_int64(0 if cov is None else _ld(cov)),
+                                  None if pcov is None else _ptr(pcov), ctypes.c_int64(0 if pcov is None else _ld(pcov)),
+                                  ctypes.c_int(prec), ctypes.c_int(convention),
+                                  None if rcs_db is None else _ptr(rcs_db), None if var_db is None else _ptr(var_db),
+                                  None if var_f is None else _ptr(var_f), _stream(stream)))
+    return rcs_db, var_db, var_f
+
+
+def debug_set_wait_limit(polls: int):
+    """fosb_debug_set_wait_limit: poll limit of the bounded panel-barrier and sweep-flag
+    waits on the current device (polls <= 0 restores the default)."""
+    _check(lib().fosb_debug_set_wait_limit(ctypes.c_int64(polls)))

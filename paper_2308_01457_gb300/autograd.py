@@ -8,8 +8,6 @@ The factorisation is kept from forward to backward (it is reused for the adjoint
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import torch
 
@@ -18,7 +16,8 @@ from . import MIXED, assemble_efie, factor, incidence, mesh_create, rcs_monostat
 
 class FosbRCS(torch.autograd.Function):
     """sigma = FosbRCS.apply(verts, tris, k, d, p, db): verts (V x 3, float64, any device)
-    -> sigma (n, float64 on verts.device); db=True returns 10 log10(sigma)."""
+    -> sigma (n, float64 on verts.device); db=True returns RCS_dB = 10 log10(sigma) (the
+    conversion and its chain rule run in the library)."""
 
     @staticmethod
     def forward(ctx, verts, tris, k, d, p, db=False):
@@ -35,16 +34,14 @@ class FosbRCS(torch.autograd.Function):
         lu = factor(Z, prec=MIXED)
         U = torch.empty_like(b)
         solve(lu, b, U)
-        sig = rcs_monostatic(mesh, k, inc, U)
-        ctx.state = (mesh, lu, Z, U, inc, k, sig, bool(db), verts.device)
-        out = 10.0 * np.log10(sig) if db else sig
+        out = rcs_monostatic(mesh, k, inc, U, db=bool(db))
+        ctx.state = (mesh, lu, Z, U, inc, k, bool(db), verts.device)
         return torch.tensor(out, dtype=torch.float64, device=verts.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        mesh, lu, Z, U, inc, k, sig, db, vdev = ctx.state
+        mesh, lu, Z, U, inc, k, db, vdev = ctx.state
         g = grad_out.detach().to("cpu", torch.float64).numpy()
-        w = g * (10.0 / math.log(10.0)) / sig if db else g
         grad = torch.zeros((mesh.nv, 3), dtype=torch.float64, device=Z.device)
-        rcs_monostatic(mesh, k, inc, U, lu=lu, weights=w, grad=grad)
+        rcs_monostatic(mesh, k, inc, U, lu=lu, weights=g, grad=grad, db=db)
         return grad.to(vdev), None, None, None, None, None

@@ -390,12 +390,19 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
   return FOSB_OK;
 }
 
+fosb_status fosb_debug_set_wait_limit(int64_t polls) {
+  FOSB_CUDA(set_wait_limit_panels(polls));
+  FOSB_CUDA(set_wait_limit_sweeps(polls));
+  return FOSB_OK;
+}
+
 fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb_quad_opts* opts, const double* inc,
-                                int64_t n_inc, const void* U, int64_t ldu, const double* weights, double* sigma,
+                                int64_t n_inc, const void* U, int64_t ldu, const double* weights, int db, double* sigma,
                                 double* grad, void* stream) {
   if (!mesh || !inc || !U || n_inc <= 0 || ldu < n_inc) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: bad arguments");
   if (!(k > 0)) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: k must be > 0");
   if (grad && (!lu || !weights)) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: gradient needs lu and weights");
+  if (db != 0 && db != 1) return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: db must be 0 or 1");
   if (lu && (lu->prec == FOSB_FP32 || lu->n != mesh->d.ne))
     return fail(FOSB_ERR_INVALID_ARG, "fosb_rcs_monostatic: lu must be an FP64 or MIXED factorisation of this mesh");
   const int nss = opts && opts->n_ss > 0 ? opts->n_ss : 5;
@@ -430,14 +437,19 @@ fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb
     }
     sig[i] = s2 / (4.0 * M_PI);
   }
-  if (sigma) std::memcpy(sigma, sig.data(), sizeof(double) * n);
+  if (sigma) {
+    for (int64_t i = 0; i < n; ++i) sigma[i] = db ? 10.0 * std::log10(sig[i]) : sig[i];
+  }
   if (!grad) return FOSB_OK;
+  // weights are dL/dsigma_i, or dL/dRCS_dB_i with db = 1: dRCS_dB/dsigma = 10 / (sigma ln 10)
+  std::vector<double> w(n);
+  for (int64_t i = 0; i < n; ++i) w[i] = db ? weights[i] * 10.0 / (sig[i] * std::log(10.0)) : weights[i];
   // Adjoint: dsigma_i = (2/(4 pi)) Re[conj(F_i).(dA_i u_i + A_i du_i)], du_i = Z^{-1}(db_i - dZ u_i);
   // with c_i = w_i (2/(4 pi)) conj(F_i) and lambda_i = Z^{-1} A_i^T c_i (Z^T = Z):
   //   sum_i w_i dsigma_i = Re[sum_i c_i.dA_i u_i + lambda_i^T db_i - lambda_i^T dZ u_i].
   std::vector<double> Cm(2 * nd3 * n, 0.0), pw(11 * 2 * n);
   for (int64_t i = 0; i < n; ++i) {
-    double sc = weights[i] * 2.0 / (4.0 * M_PI);
+    double sc = w[i] * 2.0 / (4.0 * M_PI);
     double cr[3], ci[3];
     for (int c = 0; c < 3; ++c) {
       cr[c] = sc * Fr[3 * i + c];

@@ -219,6 +219,13 @@ cudaError_t axpy_c64_into_c128(const void* d, int64_t rows, int64_t cols, int64_
 // out = (accumulate ? out : 0) + w (M + op(M)) for a square n x n matrix M (op = OP_T or OP_C)
 cudaError_t add_mirrored(const void* M, int64_t n, int64_t ldm, int op, double w, bool accumulate, bool c64, void* out,
                          int64_t ldo, cudaStream_t s);
+// Poll limits of the bounded device waits on the current device (polls <= 0: default):
+// panel grid barriers (linalg.cu) and streaming-sweep flags (trsv_stream.cu).
+cudaError_t set_wait_limit_panels(long long polls);
+cudaError_t set_wait_limit_sweeps(long long polls);
+// Largest n that the external-scratch panel path can factor with at most max_ctas CTAs on
+// the current device (co-resident panel CTAs x rows a CTA can hold).
+fosb_status getrf_external_max_n(int64_t max_ctas, int64_t* max_n);
 // row-wise inf-norm reductions: out[0] = max_i sum_j |Re|+|Im| (matrix), or max |.|
 cudaError_t norm_inf_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s);
 cudaError_t absmax_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, double* d_out, cudaStream_t s);

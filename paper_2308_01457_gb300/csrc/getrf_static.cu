@@ -13,8 +13,9 @@
 // until the process exits.  In host code the array's name is only a host-side stand-in,
 // so its device address is looked up once per device with cudaGetSymbolAddress -- on the
 // first call on that device, with that device current -- and passed to the kernels.
-// That first call on a device should therefore come before any stream capture.  All
-// calls share the array: calls whose work overlaps on the GPU race, so serialise them.
+// Every call reads its status word back with a stream synchronisation, so no call can
+// run inside a stream capture.  All calls share the array: calls whose work overlaps on
+// the GPU race, so serialise them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,12 +63,13 @@ extern "C" fosb_status fosb_getrf_static(void* A, int64_t n, int64_t lda, int pr
   static_assert(kStatusOffset + sizeof(int) <= 256, "status word must sit in the zeroed head");
   if (getrf_scratch_bytes(kStaticMaxCtas, c128) > kStaticScratchBytes)
     return fail(FOSB_ERR_INVALID_ARG, "fosb_getrf_static: scratch layout exceeds the static array");
-  // size limit: the panel kernel keeps at most 2048 rows per CTA and uses at most
-  // kStaticMaxCtas CTAs here (fewer if fewer are co-resident on this GPU)
-  const int64_t max_n = kStaticMaxCtas * 2048;
+  // size limit: the first panel holds all n rows in at most min(SM count, kStaticMaxCtas)
+  // co-resident CTAs of at most 2048 rows each (311,296 on a 152-SM GB300)
+  int64_t max_n = 0;
+  FOSB_TRY(getrf_external_max_n(kStaticMaxCtas, &max_n));
   if (n > max_n)
     return fail(FOSB_ERR_INVALID_ARG, "fosb_getrf_static: n = " + std::to_string(n) + " exceeds the limit " +
-                                          std::to_string(max_n) + " of the static scratch (use fosb_factor)");
+                                          std::to_string(max_n) + " of the static scratch on this GPU (use fosb_factor)");
   void* scratch = nullptr;
   FOSB_TRY(scratch_for_current_device(&scratch));
   cudaStream_t s = static_cast<cudaStream_t>(stream);

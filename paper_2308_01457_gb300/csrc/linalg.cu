@@ -552,6 +552,9 @@ static_assert(sizeof(PanelScratch) <= 256, "the panel header must fit the zeroed
 constexpr int kPanelThreads = 256;
 constexpr int kMaxPanelRows = 2048;  // rows per CTA (multipliers kept in shared memory)
 constexpr long long kSpinLimit = 1ll << 26;
+// Poll limit of the bounded grid-barrier waits on this device (kSpinLimit unless changed by
+// fosb_debug_set_wait_limit, which failure-detection tests use to make the waits give up).
+__device__ long long g_wait_limit = kSpinLimit;
 
 __device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* status) {
   __shared__ int ok;
@@ -568,8 +571,9 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, i
       atomicAdd(gen, 1u);
     } else {
       long long spins = 0;
+      const long long limit = g_wait_limit;
       while (*vgen == my_gen) {
-        if (++spins > kSpinLimit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
+        if (++spins > limit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
           atomicExch(status, FOSB_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -585,7 +589,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, i
 
 // Grid barrier on a counter that only grows: every CTA adds one and waits until the count
 // reaches target (this launch's base + (column + 1) x CTAs), so no CTA has to reset it.
-// Bounded: after kSpinLimit polls the status word is set to FOSB_ERR_TIMEOUT and the CTA
+// Bounded: after g_wait_limit polls the status word is set to FOSB_ERR_TIMEOUT and the CTA
 // leaves.
 __device__ bool grid_arrive_wait(unsigned* count, unsigned target, int* status) {
   __shared__ int ok;
@@ -596,8 +600,9 @@ __device__ bool grid_arrive_wait(unsigned* count, unsigned target, int* status) 
     atomicAdd(count, 1u);
     volatile unsigned* vc = count;
     long long spins = 0;
+    const long long limit = g_wait_limit;
     while (int(*vc - target) < 0) {
-      if (++spins > kSpinLimit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
+      if (++spins > limit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
         atomicExch(status, FOSB_ERR_TIMEOUT);
         ok = 0;
         break;
@@ -1391,6 +1396,15 @@ fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ip
   return FOSB_OK;
 }
 
+fosb_status getrf_external_max_n(int64_t max_ctas, int64_t* max_n) {
+  int dev = 0, nsm = 0;
+  FOSB_CUDA(cudaGetDevice(&dev));
+  FOSB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // the first panel holds all n rows in at most min(SMs, max_ctas) CTAs of kMaxPanelRows rows
+  *max_n = std::min<int64_t>(nsm, max_ctas) * kMaxPanelRows;
+  return FOSB_OK;
+}
+
 template fosb_status getrf_external_scratch<double>(void*, int64_t, int64_t, int32_t*, int*, void*, int64_t,
                                                     cudaStream_t);
 template fosb_status getrf_external_scratch<float>(void*, int64_t, int64_t, int32_t*, int*, void*, int64_t,
@@ -1526,6 +1540,13 @@ cudaError_t absmax_c128(const void* A, int64_t rows, int64_t cols, int64_t lda, 
   if (rows * cols == 0) return cudaSuccess;
   col_absmax_kernel<<<cdiv(rows * cols, 256), 256, 0, s>>>(static_cast<const double2*>(A), rows, cols, lda, d_out);
   return launched();
+}
+
+// Sets the poll limit of the panel grid-barrier waits on the current device (polls <= 0:
+// the default).
+cudaError_t set_wait_limit_panels(long long polls) {
+  const long long v = polls > 0 ? polls : kSpinLimit;
+  return cudaMemcpyToSymbol(g_wait_limit, &v, sizeof(v));
 }
 
 }  // namespace fosb

@@ -24,6 +24,9 @@ namespace {
 
 constexpr int kTB = 64;                         // rows per block
 constexpr long long kFlagSpinLimit = 1ll << 26;
+// Poll limit of the flag waits on this device (kFlagSpinLimit unless changed by
+// fosb_debug_set_wait_limit).
+__device__ long long g_flag_wait_limit = kFlagSpinLimit;
 
 __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {  // acc += a b
   acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
@@ -195,8 +198,9 @@ __global__ void __launch_bounds__(256, 2) trsv_stream_kernel(const float2* __res
       if (t == 0) {
         const volatile int* f = flags + jb * chunks + ch;
         long long spins = 0;
+        const long long limit = g_flag_wait_limit;
         while (*f == 0) {
-          if (++spins > kFlagSpinLimit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
+          if (++spins > limit || *(volatile int*)status == FOSB_ERR_TIMEOUT) {
             atomicExch(status, FOSB_ERR_TIMEOUT);
             s_abort = 1;
             break;
@@ -329,6 +333,12 @@ cudaError_t trsv_stream_c64(const void* LU, int64_t n, int64_t ld, const void* D
   }
 #undef FOSB_TS
   return launched();
+}
+
+// Sets the poll limit of the sweep flag waits on the current device (polls <= 0: the default).
+cudaError_t set_wait_limit_sweeps(long long polls) {
+  const long long v = polls > 0 ? polls : kFlagSpinLimit;
+  return cudaMemcpyToSymbol(g_flag_wait_limit, &v, sizeof(v));
 }
 
 }  // namespace fosb

@@ -11,7 +11,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (ASM_FP64, COV_GAUSS, FP32, MIXED, assemble_efie, covariance, factor, farfield_moments, incidence,
-               mesh_create, solve)
+               mesh_create, rcs_moments, solve)
 
 
 def index_sets(L0: int, L: int):
@@ -114,9 +114,10 @@ class FOSBProblem:
         return st
 
     def run(self, timers=None):
-        """Full step: nominal solves on all levels, the mean far field on level L, and the
-        CT far-field covariance (and pseudo-covariance if requested).  Returns device
-        tensors (F_mean (3 n_dir x 1), Cov (3 n_dir x 3 n_dir)[, PCov])."""
+        """Full step: nominal solves on all levels, the mean far field on level L, the CT
+        far-field covariance (and pseudo-covariance if requested) and the RCS moments
+        (self.rcs_db, self.var_f, and self.var_db with the pseudo-covariance).  Returns
+        device tensors (F_mean (3 n_dir x 1), Cov (3 n_dir x 3 n_dir)[, PCov])."""
         import torch
 
         nd3 = 3 * self.dirs.shape[0]
@@ -145,6 +146,13 @@ class FOSBProblem:
                                  prec=self.prec,
                                  pseudo=pseudo, accumulate=not first)
             first = False
+        # A11: RCS_dB of the mean field and the variance of every far-field component; with the
+        # pseudo-covariance also the delta-method variance of RCS_dB (device float64 tensors)
+        n_dir = self.dirs.shape[0]
+        self.rcs_db = torch.empty(n_dir, dtype=torch.float64, device=dev)
+        self.var_f = torch.empty(nd3, dtype=torch.float64, device=dev)
+        self.var_db = torch.empty(n_dir, dtype=torch.float64, device=dev) if pcov is not None else None
+        rcs_moments(n_dir, F, cov, pcov, rcs_db=self.rcs_db, var_db=self.var_db, var_f=self.var_f, prec=self.prec)
         if timers is not None:
             cov_end = torch.cuda.Event(enable_timing=True)
             cov_end.record()

@@ -83,6 +83,18 @@ def test_plain_fp64_full_tensor_and_rcs_moments(F):
     var_o = O.rcs_variance_db(Fo.reshape(-1, 3), covo, pcovo)
     assert np.all(var >= 0.0) and _rel(var, var_o) < 1e-7
     assert np.abs(O.rcs_db(f) - O.rcs_db(Fo.reshape(-1, 3))).max() < 1e-8
+    # the library's RCS moments (fosb_rcs_moments) against the oracle's, from the oracle's moments
+    nd = xh.shape[0]
+    r_db = torch.zeros(nd, dtype=torch.float64, device=DEV)
+    v_db = torch.zeros(nd, dtype=torch.float64, device=DEV)
+    v_f = torch.zeros(3 * nd, dtype=torch.float64, device=DEV)
+    F.rcs_moments(nd, Fm, cov, pcov, rcs_db=r_db, var_db=v_db, var_f=v_f)
+    rcs_o = O.rcs_db(Fo.reshape(-1, 3))
+    assert np.abs(r_db.cpu().numpy() - rcs_o).max() < 1e-8 * np.abs(rcs_o).max()
+    assert _rel(v_db.cpu().numpy(), var_o) < 1e-8
+    assert _rel(v_f.cpu().numpy(), np.diag(covo).real) < 1e-8
+    F.rcs_moments(nd, Fm, rcs_db=r_db, convention=1)  # the printed 4 pi |F|^2: + 10 log10((4 pi)^2)
+    assert np.abs(r_db.cpu().numpy() - rcs_o - 20 * math.log10(4 * math.pi)).max() < 1e-10
     # the mean field against the Mie series (discretisation error at 320 triangles)
     assert _rel(f, mie.farfield(k, 1.0, xh)) < 0.06
 
@@ -198,6 +210,14 @@ def test_torus_fullsize_samples_and_identities(F, torus_run):
     assert np.linalg.norm(pv - pv.T) <= 1e-12 * np.linalg.norm(pv)
     var = O.rcs_variance_db(Fm.cpu().numpy()[:, 0].reshape(-1, 3), cv, pv)
     assert np.all(np.isfinite(var))
+    # the library's RCS moments on the same GPU moments (361 directions, 30720 unknowns)
+    nd = dirs.shape[0]
+    r_db = torch.zeros(nd, dtype=torch.float64, device=DEV)
+    v_db = torch.zeros(nd, dtype=torch.float64, device=DEV)
+    F.rcs_moments(nd, Fm, cov, pcov, rcs_db=r_db, var_db=v_db)
+    assert _rel(v_db.cpu().numpy(), var) < 1e-12
+    rcs_o = O.rcs_db(Fm.cpu().numpy()[:, 0].reshape(-1, 3))
+    assert np.abs(r_db.cpu().numpy() - rcs_o).max() < 1e-12 * np.abs(rcs_o).max()
     # the duplicated endpoint of the 361 directions: F(0) = F(2 pi)
     f = Fm.cpu().numpy()[:, 0].reshape(-1, 3)
     assert np.abs(f[0] - f[-1]).max() <= 1e-12 * np.abs(f).max()

@@ -86,8 +86,10 @@ def test_static_lu_matches_allocating_entry_point(F, prec_name, tol):
 def test_static_lu_rejects_sizes_beyond_its_scratch(F):
     A = torch.zeros((2, 2), dtype=torch.complex128, device="cuda")
     piv = torch.zeros(2, dtype=torch.int32, device="cuda")
-    n = 524288 + 1
-    st = F.lib().fosb_getrf_static(ctypes.c_void_p(A.data_ptr()), ctypes.c_int64(n), ctypes.c_int64(n),
-                                   ctypes.c_int(F.FP64), ctypes.c_void_p(piv.data_ptr()), None)
-    assert st == F.FOSB_ERR_INVALID_ARG
-    assert b"exceeds" in F.lib().fosb_last_error()
+    # the limit: min(SM count, 256) panel CTAs of at most 2048 rows (311,296 on 152 SMs)
+    n_max = min(torch.cuda.get_device_properties(0).multi_processor_count, 256) * 2048
+    for n in (n_max + 1, 524288 + 1):
+        st = F.lib().fosb_getrf_static(ctypes.c_void_p(A.data_ptr()), ctypes.c_int64(n), ctypes.c_int64(n),
+                                       ctypes.c_int(F.FP64), ctypes.c_void_p(piv.data_ptr()), None)
+        assert st == F.FOSB_ERR_INVALID_ARG
+        assert f"exceeds the limit {n_max}".encode() in F.lib().fosb_last_error()
