@@ -9,7 +9,9 @@ angles, and the combination-technique far-field covariance over L0 = 0, L = 4 (b
 Prints one JSON line.  `value` is the device-timed seconds per FOSB step with the
 meshes resident on the GPU (lower is better); `e2e` is the same step through the
 public API from host arrays (mesh upload, result download).  `--impl reference` times
-the FP64 CPU oracle on bounded samples of the same workload and extrapolates.
+the FP64 CPU oracle: a complete oracle step one level below the workload's finest,
+measured end to end, extended to the workload by a cost model whose error is measured
+one level further down.
 """
 from __future__ import annotations
 
@@ -297,7 +299,7 @@ def run_fosb(args):
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(W, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(W)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -378,80 +380,168 @@ def run_e2e(args, W, meshes, dirs, arith):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(W, budget_s: float = 20.0):
-    """FP64 CPU oracle, as it stands, on bounded samples of the workload: the assembly
-    rate (entries/s) from a full oracle assembly of a sample level, the dense LU rate
-    from numpy/LAPACK at a sample size; the full step is extrapolated with O(N^2)
-    assembly and O(N^3) factorisations (the oracle re-factors per covariance block)."""
+def _sizes(W, l):
+    """(N, V) of level l: icosphere level l + 1 (sphere) or the torus grid 10*2^(l-1) x 4*2^(l-1)."""
+    if W["mesh"] == "torus":
+        return 120 * 4 ** (l - 1), 40 * 4 ** (l - 1)
+    return 120 * 4**l, 40 * 4**l + 2
+
+
+def _ct_blocks(L0, L):
+    """The blocks the combination technique solves (l1 >= l2 on Lambda_+ and Lambda_-)."""
+    plus = [(a, L + L0 - a) for a in range(L0, L + 1) if L0 <= L + L0 - a <= L]
+    minus = [(a, L + L0 - 1 - a) for a in range(L0, L + 1) if L0 <= L + L0 - 1 - a <= L]
+    return [b for b in plus + minus if b[0] >= b[1]]
+
+
+def oracle_step(W, L):
+    """One complete FOSB step of the FP64 CPU oracle, as it stands, on levels L0..L of the
+    workload: per level the steps of oracle.nominal_level (assembly, plane-wave RHS, LAPACK
+    solve, far-field matrix, SD right-hand side), each timed, then the CT far-field
+    covariance over L0..L (oracle.ct_farfield_covariance).  Returns (F_mean, cov, times)."""
     import oracle as O
     import fosb_synth as S
 
     O.build()
-    cores = O.n_threads()
-    t_begin = time.perf_counter()
-    def mesh(lvl):
-        return O.from_synth(S.icosphere(lvl) if W["mesh"] == "sphere" else S.torus(10 * 2 ** (lvl - 1), 4 * 2 ** (lvl - 1)))
+    xh = _dirs(W)
+    meshes = (S.torus_hierarchy(list(range(W["L0"], L + 1))) if W["mesh"] == "torus"
+              else [S.icosphere(l + 1) for l in range(W["L0"], L + 1)])
+    times = {"levels": {}, "ct": 0.0}
+    t_all = time.perf_counter()
+    lev = {}
+    for l, sm in zip(range(W["L0"], L + 1), meshes):
+        m = O.from_synth(sm)
+        tl = {}
+        t = time.perf_counter()
+        Z = O.assemble_z(m, W["k"])
+        tl["asm"] = time.perf_counter() - t
+        t = time.perf_counter()
+        b = O.rhs_planewave(m, W["k"], W["d"], W["p"])[:, 0]
+        u = O.solve(Z, b)
+        tl["solve"] = time.perf_counter() - t
+        t = time.perf_counter()
+        A = O.farfield_matrix(m, W["k"], xh)
+        B = O.sd_rhs(m, W["k"], u)
+        tl["maps"] = time.perf_counter() - t
+        lev[l] = O.Level(m, Z, u, A, B)
+        times["levels"][l] = tl
+    t = time.perf_counter()
+    cov = O.ct_farfield_covariance(lev, W["L0"], L, W["kernel"], W["sigma"], W["ell"])
+    times["ct"] = time.perf_counter() - t
+    times["total"] = time.perf_counter() - t_all
+    return lev[L].A @ lev[L].u, cov, times
 
-    # assembly sample: successively larger levels while the next one, predicted from the
-    # rate just measured, fits in about half of the budget
-    asm_rate, asm_lvl = None, None
-    for lvl in (2, 3, 4):
-        m = mesh(lvl)
-        if asm_rate is not None and (time.perf_counter() - t_begin) + m.n_edges**2 / asm_rate > 0.5 * budget_s:
-            break
-        t0 = time.perf_counter()
-        O.assemble_z(m, W["k"])
-        asm_rate, asm_lvl = m.n_edges**2 / (time.perf_counter() - t0), lvl
-    # LU sample: the same, up to N = 7680, within the whole budget
-    rng = np.random.default_rng(0)
-    lu_rate, n_lu = None, None
-    for n in (1920, 3840, 7680):
-        if lu_rate is not None and (time.perf_counter() - t_begin) + (8.0 / 3.0) * n**3 / lu_rate > budget_s:
-            break
-        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
-        b = rng.standard_normal((n, 1)) + 0j
-        t0 = time.perf_counter()
-        np.linalg.solve(A, b)
-        lu_rate, n_lu = (8.0 / 3.0) * n**3 / (time.perf_counter() - t0), n
-    N = {l: _n_edges(W, l) for l in W["levels"]}
-    t_asm = sum(N[l] ** 2 / asm_rate for l in N)
-    t_lu = lambda n: (8.0 / 3.0) * n**3 / lu_rate  # noqa: E731
-    t_nominal = sum(t_lu(N[l]) for l in N)
-    t_cov = 0.0
-    plus = [(a, W["L"] + W["L0"] - a) for a in W["levels"]]
-    minus = [(a, W["L"] + W["L0"] - 1 - a) for a in W["levels"]]
-    for (a, c) in [x for x in plus if x[0] >= x[1] and x[1] in N] + [x for x in minus if x[0] >= x[1] and x[1] in N]:
-        t_cov += t_lu(N[a]) + t_lu(N[c]) + 8.0 * (N[a] ** 2 * N[c] + N[c] ** 2 * N[a]) / lu_rate
-    total = t_asm + t_nominal + t_cov
-    return {"value": round(total, 2), "unit": "s per FOSB step", "cores": cores, "kind": "oracle",
-            "sample": f"oracle assembly of the level-{asm_lvl} mesh ({asm_rate:.3e} entries/s) and LAPACK complex LU "
-                      f"at N={n_lu} ({lu_rate / 1e9:.1f} GFLOP/s), extrapolated to the full step "
-                      f"(N^2 assembly, N^3 factorisations); sample time {time.perf_counter() - t_begin:.1f} s",
-            "assembly_entries_per_s": round(asm_rate, 1)}
+
+def _lu_flops(n):
+    return (8.0 / 3.0) * float(n) ** 3
+
+
+def lapack_rate(n, seed=0):
+    """Flop rate of the oracle's dense solve (numpy.linalg.solve: LAPACK LU and one right-
+    hand side) on a seeded random complex n x n system, counted as 8/3 n^3."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    b = rng.standard_normal(n) + 0j
+    t = time.perf_counter()
+    np.linalg.solve(A, b)
+    return _lu_flops(n) / (time.perf_counter() - t)
+
+
+def _ct_flops(W, L):
+    """Flops of the oracle's CT covariance over L0..L: per block the two LAPACK solves
+    (a factorisation of each Z and the triangular solves), C = B1 K B2^H with dense B, and
+    the far-field product A1 Sigma A2^H."""
+    nd3 = 3 * W["n_dir"]
+    f = 0.0
+    for l1, l2 in _ct_blocks(W["L0"], L):
+        (n1, v1), (n2, v2) = _sizes(W, l1), _sizes(W, l2)
+        f += _lu_flops(n1) + _lu_flops(n2) + 8.0 * (n1 * n1 * n2 + n2 * n2 * n1)
+        f += 8.0 * (n1 * v1 * v2 + n1 * v2 * n2) + 8.0 * (nd3 * n1 * n2 + nd3 * nd3 * n2)
+    return f
+
+
+def oracle_model(W, times, L, rate):
+    """Predicted oracle time of the step over L0..L from a measured step over L0..L-1:
+    the measured levels as measured; level L's assembly scaled by N^2 (point pairs) and its
+    far-field and SD maps by N from level L-1; level L's LAPACK solve and the whole CT
+    covariance over L0..L by their flop counts at `rate` (a LAPACK solve measured at half
+    of level L's N)."""
+    lv = times["levels"]
+    total = sum(sum(t.values()) for t in lv.values())
+    r = _sizes(W, L)[0] / _sizes(W, L - 1)[0]
+    total += lv[L - 1]["asm"] * r * r + lv[L - 1]["maps"] * r + _lu_flops(_sizes(W, L)[0]) / rate
+    return total + _ct_flops(W, L) / rate
+
+
+def cpu_baseline(W, with_outputs=False):
+    """The FP64 CPU oracle, as it stands, on the machine's host cores: a complete oracle step
+    one level below the workload's finest (every level's assembly, solve and maps and the
+    full CT covariance, measured end to end), extended to the workload by oracle_model
+    with a LAPACK rate measured at half the finest N.  The model's error is measured one
+    level down: the step two levels below, with a LAPACK rate at half of the next N,
+    predicts the measured step."""
+    cores = len(os.sched_getaffinity(0))
+    L = W["L"]
+    _, _, t_cal = oracle_step(W, L - 2)
+    F, cov, t_meas = oracle_step(W, L - 1)
+    r_cal = lapack_rate(_sizes(W, L - 1)[0] // 2)
+    rate = lapack_rate(_sizes(W, L)[0] // 2)
+    pred_meas = oracle_model(W, t_cal, L - 1, r_cal)
+    value = oracle_model(W, t_meas, L, rate)
+    n_f = _sizes(W, L - 1)[0]
+    res = {"value": round(value, 2), "unit": "s per FOSB step", "cores": cores, "kind": "oracle",
+           "sample": f"complete oracle step over levels {W['L0']}..{L - 1} (N <= {n_f}) measured end to end in "
+                     f"{t_meas['total']:.1f} s; modelled: level {L} (assembly x N^2, maps x N) and the LAPACK "
+                     f"solves of level {L} and of the CT covariance (flop count at {rate / 1e9:.1f} GFLOP/s, "
+                     f"a LAPACK solve measured at N = {_sizes(W, L)[0] // 2})",
+           "measured_step": {"levels": [W["L0"], L - 1], "s": round(t_meas["total"], 2),
+                             "ct_covariance_s": round(t_meas["ct"], 2),
+                             "assembly_finest_s": round(t_meas["levels"][L - 1]["asm"], 2),
+                             "assembly_entries_per_s": round(n_f * n_f / t_meas["levels"][L - 1]["asm"], 1)},
+           "model_error": {"predicted_s": round(pred_meas, 2), "measured_s": round(t_meas["total"], 2),
+                           "rel": round(pred_meas / t_meas["total"] - 1.0, 3),
+                           "note": f"the model on the step over {W['L0']}..{L - 2} with a LAPACK rate at "
+                                   f"N = {_sizes(W, L - 1)[0] // 2}, against the measured step"}}
+    return (res, F, cov) if with_outputs else res
 
 
 def run_reference(args):
+    """The reference arm: no upstream implementation exists (the paper's Bempp scripts are
+    not provided), so it is the FP64 CPU oracle.  Each timed step measures the complete
+    oracle step one level below the workload's finest and extends it to the workload with
+    oracle_model (the LAPACK rate at half the finest N is measured once, before the steps);
+    warm-up steps run the step two levels below."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     W = WORKLOADS[args.workload]
-    vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(W, budget_s=min(args.cpu_budget, 10.0))
+    L = W["L"]
     t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        _, _, cal = oracle_step(W, L - 2)
+    rate = lapack_rate(_sizes(W, L)[0] // 2)
+    vals, meas = [], []
     for _ in range(args.steps):
-        r = cpu_baseline(W, budget_s=min(args.cpu_budget, 10.0))
-        vals.append(r["value"])
-    v = statistics.median(vals)
-    r["value"] = v
+        _, _, t = oracle_step(W, L - 1)
+        vals.append(oracle_model(W, t, L, rate))
+        meas.append(t["total"])
+    v = round(statistics.median(vals), 2)
+    pred = oracle_model(W, cal, L - 1, lapack_rate(_sizes(W, L - 1)[0] // 2))
+    wall = time.perf_counter() - t_all
+    cb = {"value": v, "unit": "s per FOSB step", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+          "sample": f"each step: the complete oracle step over levels {W['L0']}..{L - 1} measured end to end "
+                    f"(median {statistics.median(meas):.1f} s), extended to level {L} by the model at "
+                    f"{rate / 1e9:.1f} GFLOP/s (LAPACK solve measured at N = {_sizes(W, L)[0] // 2})",
+          "model_error": {"predicted_s": round(pred, 2), "measured_s": round(statistics.median(meas), 2),
+                          "rel": round(pred / statistics.median(meas) - 1.0, 3)}}
     line = {"metric": METRIC, "value": v, "unit": "s per FOSB step", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "levels": W["levels"], "k": W["k"], "n_dir": W["n_dir"],
                        "ct": [W["L0"], W["L"]], "parallelism": "host cores"},
-            "cpu_baseline": r,
+            "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "s per FOSB step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "sample_wall_s": round(time.perf_counter() - t_all, 1)}
+            "measured_wall_s": round(wall, 1)}
     print(json.dumps(line), flush=True)
 
 
@@ -467,7 +557,6 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":

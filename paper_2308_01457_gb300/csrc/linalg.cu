@@ -652,6 +652,10 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::ty
   __shared__ V s_l[kMaxPanelRows];
   __shared__ V s_piv[64];
   __shared__ int64_t s_p;
+  // identity pivots first: if a barrier wait gives up, the columns not reached keep valid rows
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < jb; c += blockDim.x) ipiv[c] = int32_t(row_base + c);
+  __syncthreads();
 #define ROW(r, c) A[(r) * lda + (c)]
   for (int j = 0; j < jb; ++j) {
     const int par = j & 1;
@@ -683,7 +687,9 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(typename C2<T>::ty
     // 3. the winning key names the pivot row and, through the row partition, its CTA
     if (threadIdx.x == 0) {
       const unsigned long long key = *reinterpret_cast<volatile unsigned long long*>(&scr->key[(row_base + j) & 3]);
-      s_p = int64_t(0xFFFFFFFFu - unsigned(key & 0xFFFFFFFFull));
+      // an exactly zero column folds no key: no interchange (status SINGULAR below)
+      const int64_t pk = int64_t(0xFFFFFFFFu - unsigned(key & 0xFFFFFFFFull));
+      s_p = (key == 0ull || pk >= m) ? int64_t(j) : pk;
       if (blockIdx.x == 0) {
         ipiv[j] = int32_t(row_base + s_p);
         if ((key >> 32) == 0ull) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
@@ -751,6 +757,9 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(typename C2<T
   __shared__ unsigned long long s_key[kPanelThreads / 32];
   __shared__ V s_piv[64];
   __shared__ int64_t s_p;
+  // identity pivots first: if a barrier wait gives up, the columns not reached keep valid rows
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < jb; c += blockDim.x) ipiv[c] = int32_t(row_base + c);
   for (int e = threadIdx.x; e < nr * jb; e += blockDim.x) sP[e] = A[(lo + e / jb) * lda + e % jb];
   __syncthreads();
 #define ROW(r, c) sP[((r) - lo) * jb + (c)]
@@ -783,7 +792,9 @@ __global__ void __launch_bounds__(kPanelThreads) panel_smem_kernel(typename C2<T
     // 3. the winning key names the pivot row and, through the row partition, its CTA
     if (threadIdx.x == 0) {
       const unsigned long long key = *reinterpret_cast<volatile unsigned long long*>(&scr->key[(row_base + j) & 3]);
-      s_p = int64_t(0xFFFFFFFFu - unsigned(key & 0xFFFFFFFFull));
+      // an exactly zero column folds no key: no interchange (status SINGULAR below)
+      const int64_t pk = int64_t(0xFFFFFFFFu - unsigned(key & 0xFFFFFFFFull));
+      s_p = (key == 0ull || pk >= m) ? int64_t(j) : pk;
       if (blockIdx.x == 0) {
         ipiv[j] = int32_t(row_base + s_p);
         if ((key >> 32) == 0ull) atomicCAS(status, 0, FOSB_ERR_SINGULAR);
@@ -834,7 +845,7 @@ __global__ void laswp_kernel(typename C2<T>::type* A, int64_t n, int64_t lda, in
   if (c >= n || (c >= j0 && c < j0 + jb)) return;
   for (int i = 0; i < jb; ++i) {
     int64_t p = ipiv[j0 + i];
-    if (p != j0 + i) {
+    if (p != j0 + i && p >= 0 && p < n) {  // a pivot outside the matrix (never written) is skipped
       auto t = A[(j0 + i) * lda + c];
       A[(j0 + i) * lda + c] = A[p * lda + c];
       A[p * lda + c] = t;
