@@ -312,6 +312,14 @@ fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb
  * wait ran out leaves its outputs unspecified; destroy and recreate its handle. */
 fosb_status fosb_debug_set_wait_limit(int64_t polls);
 
+/* Throughput microbenchmarks of the execution units the kernels are bound by (diagnostics
+ * for roofline denominators).  kind 0: FP32 FMA pipe; 1: FP64 FMA pipe; 2: tcgen05.mma
+ * kind::tf32 (M = 128, N = 256, K = 8) back to back from shared memory, one CTA per SM; 3: the
+ * same with kind::f16 bf16 (K = 16).  Writes the best of five CUDA-event-timed launches on
+ * the legacy default stream in TFLOP/s (2 flops per multiply-add).  Allocates and frees a few
+ * bytes; synchronises the device.  Errors: FOSB_ERR_INVALID_ARG, FOSB_ERR_TIMEOUT. */
+fosb_status fosb_peak_microbench(int kind, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,7 +68,7 @@ def lib():
                      "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
                      "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
                      "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read", "fosb_rcs_moments",
-                     "fosb_debug_set_wait_limit"):
+                     "fosb_debug_set_wait_limit", "fosb_peak_microbench"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -263,3 +263,11 @@ def debug_set_wait_limit(polls: int):
     """fosb_debug_set_wait_limit: poll limit of the bounded panel-barrier and sweep-flag
     waits on the current device (polls <= 0 restores the default)."""
     _check(lib().fosb_debug_set_wait_limit(ctypes.c_int64(polls)))
+
+
+def peak_microbench(kind: str) -> float:
+    """fosb_peak_microbench: measured TFLOP/s of 'fp32' or 'fp64' FMA, or of back-to-back
+    tcgen05 'tf32' or 'bf16' MMAs (M = 128, N = 256), on the current device."""
+    out = ctypes.c_double()
+    _check(lib().fosb_peak_microbench(ctypes.c_int(["fp32", "fp64", "tf32", "bf16"].index(kind)), ctypes.byref(out)))
+    return out.value
