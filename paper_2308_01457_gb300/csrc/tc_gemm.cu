@@ -23,8 +23,8 @@ constexpr int TC_M = 128, TC_N = 128, TC_KC = 16;       // tile rows, tile compl
 constexpr int SLAB = 128 * 8 * 4;                        // bytes per k-slab of one 128-row operand part
 constexpr int PART = SLAB * (TC_KC / 8);                 // 8192 bytes per part per chunk
 constexpr int SMEM_A = 4 * PART, SMEM_B = 4 * PART;      // parts: re_b, re_s, im_b, im_s
-constexpr int EPI_LD = 65;                               // padded float2 row stride of the epilogue tile
-constexpr int SMEM_EPI = TC_M * EPI_LD * 8;              // 66560 bytes (epilogue transpose tile)
+constexpr int EPI_LD = 66;                               // padded float2 row stride of the epilogue tile (16-B rows)
+constexpr int SMEM_EPI = TC_M * EPI_LD * 8;              // 67584 bytes (epilogue tile)
 constexpr int TMEM_COLS = 256;
 constexpr long long kMmaSpinLimit = 1ll << 24;
 
@@ -118,6 +118,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(a));
 }
 __device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n)); }
+// 16-byte global -> shared copy that bypasses the registers; bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(WS_THREADS, 1)
     cgemm_update_tc_ws_kernel(int64_t M, int64_t N, int64_t K, const float2* __restrict__ A, int64_t lda,
@@ -277,6 +283,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue (128 threads)
+    // Per 64-column half of a tile: (1) the C half-tile goes to the padded shared tile by
+    // cp.async, all 4096 16-byte pieces in flight at once and, for the first half, issued
+    // before the accumulator is waited for; (2) thread r subtracts its TMEM row (lane r) in
+    // place; (3) coalesced 16-byte stores.  Without 16-byte alignment of C the tile takes the
+    // accumulator and C is updated element by element.
     const int et = tid - 9 * 32;              // 0..127
     const int lane_base = (warp & 3) * 32;    // TMEM lane group of this warp
     const int r_local = lane_base + lane;
@@ -284,60 +295,76 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tcount) {
       const int b = int(tcount & 1);
       const int64_t ub = tcount >> 1;
-      // the stop decision must be the same in all four epilogue warps (they share named
-      // barriers): a flag written before and read after one
-      if (!mbar_wait(smem_u32(&bar_tfull[b]), uint32_t(ub & 1))) {
-        fail();
-        epi_stop = 1;
-      }
-      named_bar(1, 128);
-      if (epi_stop) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t d_re = tmem + uint32_t(b) * TMEM_COLS, d_im = d_re + TC_N;
       const int64_t row0 = (tile / tiles_n) * TC_M, col0 = (tile % tiles_n) * TC_N;
+      const uint32_t d_re = tmem + uint32_t(b) * TMEM_COLS, d_im = d_re + TC_N;
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
+        if (vec_ok) {
+#pragma unroll 8
+          for (int q = 0; q < 32; ++q) {
+            const int e = et + 128 * q;  // 0 .. 4095 pairs of complex
+            const int r = e >> 5, c = (e & 31) * 2;
+            const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+            const int bytes = gr < M ? (gc + 1 < N ? 16 : (gc < N ? 8 : 0)) : 0;
+            cp_async16(smem_u32(&sE[r * EPI_LD + c]), bytes ? static_cast<const void*>(C + gr * ldc + gc) : C, bytes);
+          }
+          cp_async_commit();
+        }
+        if (h == 0) {
+          // the stop decision must be the same in all four epilogue warps (they share named
+          // barriers): a flag written before and read after one
+          if (!mbar_wait(smem_u32(&bar_tfull[b]), uint32_t(ub & 1))) {
+            fail();
+            epi_stop = 1;
+          }
+          named_bar(1, 128);
+          if (epi_stop) {
+            cp_async_wait_all();  // no copy may land after the kernel has left
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        if (vec_ok) {
+          cp_async_wait_all();
+          named_bar(1, 128);  // every thread's pieces of C are in the tile
+        }
 #pragma unroll 1
         for (int cs = 0; cs < 2; ++cs) {
           uint32_t vr[32], vi[32];
           tmem_ld32(d_re + (uint32_t(lane_base) << 16) + h * 64 + cs * 32, vr);
           tmem_ld32(d_im + (uint32_t(lane_base) << 16) + h * 64 + cs * 32, vi);
           asm volatile("tcgen05.wait::ld.sync.aligned;");
+          float2* row = sE + r_local * EPI_LD + cs * 32;
+          if (vec_ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            sE[r_local * EPI_LD + cs * 32 + j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+            for (int j = 0; j < 32; j += 2) {
+              float4 c4 = *reinterpret_cast<float4*>(row + j);
+              c4.x -= __uint_as_float(vr[j]);
+              c4.y -= __uint_as_float(vi[j]);
+              c4.z -= __uint_as_float(vr[j + 1]);
+              c4.w -= __uint_as_float(vi[j + 1]);
+              *reinterpret_cast<float4*>(row + j) = c4;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) row[j] = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+          }
         }
-        if (h == 1) {  // every accumulator value of this buffer is in registers / shared memory now
+        if (h == 1) {  // every accumulator value of this buffer has been read
           asm volatile("tcgen05.fence::before_thread_sync;");
           mbar_arrive(smem_u32(&bar_tempty[b]));
         }
         named_bar(1, 128);
         if (vec_ok) {
-#pragma unroll 1
-          for (int pass = 0; pass < 4; ++pass) {
-            float4 o[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int e = et + 128 * (q + 8 * pass);  // 0 .. 4095 pairs of complex
-              const int r = e >> 5, c = (e & 31) * 2;
-              const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
-              o[q] = (gr < M && gc + 1 < N) ? *reinterpret_cast<const float4*>(C + gr * ldc + gc)
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int e = et + 128 * (q + 8 * pass);
-              const int r = e >> 5, c = (e & 31) * 2;
-              const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
-              if (gr < M && gc + 1 < N) {
-                const float2 d0 = sE[r * EPI_LD + c], d1 = sE[r * EPI_LD + c + 1];
-                *reinterpret_cast<float4*>(C + gr * ldc + gc) =
-                    make_float4(o[q].x - d0.x, o[q].y - d0.y, o[q].z - d1.x, o[q].w - d1.y);
-              } else if (gr < M && gc < N) {
-                float2 v = C[gr * ldc + gc];
-                const float2 d0 = sE[r * EPI_LD + c];
-                C[gr * ldc + gc] = make_float2(v.x - d0.x, v.y - d0.y);
-              }
+#pragma unroll 8
+          for (int q = 0; q < 32; ++q) {
+            const int e = et + 128 * q;
+            const int r = e >> 5, c = (e & 31) * 2;
+            const int64_t gr = row0 + r, gc = col0 + h * 64 + c;
+            if (gr < M && gc + 1 < N) {
+              *reinterpret_cast<float4*>(C + gr * ldc + gc) = *reinterpret_cast<const float4*>(&sE[r * EPI_LD + c]);
+            } else if (gr < M && gc < N) {
+              C[gr * ldc + gc] = sE[r * EPI_LD + c];
             }
           }
         } else {
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             }
           }
         }
-        named_bar(1, 128);
+        named_bar(1, 128);  // the tile is free for the next half's copies
       }
     }
   }
