@@ -49,7 +49,7 @@ WORKLOADS = {
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
 # DRAM bytes (read + write) per complex64 output element of one tcgen05 LU-update launch,
 # from the ncu capture summarised in profiles/ (C is read and written once: 16 B algorithmic)
-LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (471.830272e6 + 396.855296e6) / 7552.0**2  # 15.23 B
+LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (545.124352e6 + 381.822208e6) / 7552.0**2  # 16.25 B
 
 
 def _peaks():
@@ -225,7 +225,8 @@ def run_fosb(args):
     # algorithmic work -> (bound, flops, peak, kernel, note) per family
     fam_model = {
         "lu_update": ("tensor", 1.0, tf32_peak,
-                      "cgemm_update_tc_ws_kernel (persistent warp-specialised tcgen05 kind::tf32, 3xTF32 complex)",
+                      "cgemm_update_split_kernel (persistent tcgen05 kind::tf32 N = 256, 3xTF32 complex, operands "
+                      "split once per block and bulk-copied; the split kernels are timed with it)",
                       f"TF32 dense = bf16 sustained {bf16} ({bf16_src}) x 1.1/2.25; work = useful complex flops "
                       "8MNK (3xTF32 executes 3x that on the tensor pipe, so frac <= 1/3)"),
         "asm_regular": ("alu", 27.0, fp_peak,

@@ -166,6 +166,13 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
 // timing record (fosb_profile_read): factor updates and solve sweeps are timed apart
 cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                             void* C, int64_t ldc, int* status, cudaStream_t s, const char* family = "lu_update");
+// The same update for K <= 128 with A and B split once into bulk-copy images
+// (tc_update.cu): workspaces of update_split_a_bytes(M) and update_split_b_bytes(N) bytes.
+size_t update_split_a_bytes(int64_t M);
+size_t update_split_b_bytes(int64_t N);
+cudaError_t cgemm_update_tc_split(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                                  int64_t ldb, void* C, int64_t ldc, int* status, void* ws_a, void* ws_b,
+                                  cudaStream_t s);
 // complex128 GEMM computed in float-float on the FP32 pipe (FP64-class accuracy).  A_split,
 // if given, is split_ff of A as stored (same shape, leading dimension lda).
 cudaError_t gemm_c128_ff(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha_re, double alpha_im,

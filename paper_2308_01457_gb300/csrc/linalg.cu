@@ -1271,10 +1271,16 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
   // complex64: tournament-pivoting panels (no grid-wide waits); complex128: cooperative
   // partial pivoting with one grid barrier per column
   char* tslu_scr = nullptr;
+  void* ws_a = nullptr;  // complex64: the trailing update's operands, split once per block
+  void* ws_b = nullptr;
   if constexpr (sizeof(T) == 4) {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tslu_scr), tslu_scratch_bytes(n), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&ws_a, update_split_a_bytes(n), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&ws_b, update_split_b_bytes(n), s);
     if (e != cudaSuccess) {
       cudaFreeAsync(scratch, s);
+      if (tslu_scr) cudaFreeAsync(tslu_scr, s);
+      if (ws_a) cudaFreeAsync(ws_a, s);
       return cuda_fail(e, "getrf: panel scratch");
     }
   }
@@ -1324,7 +1330,8 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
                               s);
         if (e == cudaSuccess && jb2 > 0) e = trsm_lower(Ap + jb1 * lda + jb1, jb2, Ap + jb1 * lda + jb, rest);
         if (e == cudaSuccess)
-          e = cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s);
+          e = cgemm_update_tc_split(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda,
+                                    d_status, ws_a, ws_b, s);
       }
       if (e != cudaSuccess) st = cuda_fail(e, "getrf: blocked step");
     }
@@ -1352,6 +1359,8 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
   }
   cudaFreeAsync(scratch, s);
   if (tslu_scr) cudaFreeAsync(tslu_scr, s);
+  if (ws_a) cudaFreeAsync(ws_a, s);
+  if (ws_b) cudaFreeAsync(ws_b, s);
   return st;
 }
 
