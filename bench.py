@@ -44,6 +44,10 @@ WORKLOADS = {
     # Matern-3/2 (std 0.002, l = 0.2), 361 directions in the z = 0 plane, d = x, p = z
     "torus-ka10-ct-L5": dict(mesh="torus", levels=[1, 2, 3, 4, 5], k=10.0, sigma=0.002, ell=0.2, n_dir=361, L0=1,
                              L=5, d=(1, 0, 0), p=(0, 0, 1), dirs="zplane", kernel="matern32"),
+    # batched: 64 seeded ellipsoids (semi-axes U[0.5, 1.5], k U[1, 6], icosphere level 2..4:
+    # N = 480 / 1920 / 7680), 16 Fibonacci incident directions each; assembly, complex64 LU
+    # with FP64 refinement and the 16 solves of every scatterer
+    "batched-ellipsoids-64": dict(kind="batched", n=64, n_dir=16),
 }
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
@@ -321,6 +325,174 @@ def run_fosb(args):
         torch.distributed.destroy_process_group()
 
 
+def _batched_inputs(W):
+    import fosb_synth as S
+
+    table = S.batched_ellipsoid_table(W["n"])
+    meshes = [S.ellipsoid(lvl, tuple(ax)) for ax, _, lvl in table]
+    ks = [k for _, k, _ in table]
+    d = S.fibonacci_directions(W["n_dir"])
+    p = np.asarray(S.polarisation_for(d)).reshape(-1, 3)
+    return table, meshes, ks, d, p
+
+
+def run_batched(args):
+    """The batched workload: one step = batched assembly (regular pairs of all 64 scatterers in
+    one persistent launch, tile shape from the autotuner), then the batched factorisation and
+    refined 16-column solve of every scatterer (worker streams, largest first)."""
+    import ctypes
+
+    import torch
+
+    import paper_2308_01457_gb300 as F
+    from paper_2308_01457_gb300.batched import BatchedProblem
+
+    F.build.build()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    upeaks = {kd: round(F.peak_microbench(kd), 2) for kd in ("fp32", "fp64", "tf32", "bf16")}
+    table, meshes, ks, d, p = _batched_inputs(W)
+    prob = BatchedProblem(meshes, ks, d, p).setup()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):  # the first warm-up step runs the autotuner
+        prob.run(tune=True)
+    barrier()
+    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "oz_prep", "getrs"]
+    for fam in families:
+        F.lib().fosb_profile_read(fam.encode(), None, None, None)
+    launches0 = F.lib().fosb_kernel_launches()
+    clocks = _clock_sampler(local) if rank == 0 else None
+    F.lib().fosb_profile_enable(1)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        prob.run(tune=True)
+    t1.record()
+    barrier()
+    F.lib().fosb_profile_enable(0)
+    clk = _clock_summary(clocks)
+    launches = int(F.lib().fosb_kernel_launches() - launches0)
+    fam = {}
+    for f in families:
+        ms_c, n_c, w_c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        F.lib().fosb_profile_read(f.encode(), ctypes.byref(ms_c), ctypes.byref(n_c), ctypes.byref(w_c))
+        fam[f] = (ms_c.value / args.steps, n_c.value / args.steps, w_c.value / args.steps)
+    ms = _max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, "cuda")
+    peaks = _peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    model = {"lu_update": ("tensor", 1.0, bf16 * TF32_PER_BF16, "cgemm_update_split_kernel"),
+             "asm_regular": ("alu", 27.0, upeaks["fp32"], "efie_regular_ff_batched_kernel (persistent, ticketed tiles)"),
+             "lu_panel": ("latency", 1.0, None, "tslu_gepp_kernel"),
+             "asm_singular": ("alu", 1.0, None, "efie_singular_batched_kernel"),
+             "gemm_oz": ("tensor", 1.0, bf16, "oz_gemm_kernel"), "gemm_ff": ("alu", 1.0, upeaks["fp32"], "zgemm_ff_kernel"),
+             "oz_prep": ("hbm", 1.0, peaks.get("hbm_gbs", 6800.0), "oz digit prep")}
+    dom = max((f for f in model if fam[f][0] > 0), key=lambda f: fam[f][0])
+    bound, wsc, pk, kname = model[dom]
+    unit_scale, unit = (1e9, "GB/s") if bound == "hbm" else (1e12, "TFLOP/s")
+    ach = fam[dom][2] * wsc / (fam[dom][0] * 1e-3) / unit_scale
+    roofline = {"bound": bound, "achieved": round(ach, 3), "peak": round(pk, 2) if pk else None, "unit": unit,
+                "frac": round(ach / pk, 4) if pk else None, "traffic": None, "kernel": kname, "family": dom,
+                "ms_per_step": round(fam[dom][0], 2), "launches_per_step": fam[dom][1],
+                "peak_source": "measured (MEASURED_PEAKS.json bf16 sustained x 1.1/2.25 for TF32; FP32 FMA pipe by "
+                               "fosb_peak_microbench); family times overlap across the worker streams"}
+    calls = {f: {"ms_per_step": round(v[0], 2), "launches_per_step": v[1]} for f, v in fam.items()}
+    N = [h.n_edges for h in prob.handles]
+    t_asm = fam["asm_regular"][0] + fam["asm_singular"][0]
+    e2e = run_batched_e2e(args, W) if rank == 0 and not args.no_e2e else None
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per batch step", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: float-float (f32x2) regular pairs, f64 singular pairs, 3xTF32 tensor-core LU "
+                     "(c64 factors) with FP64-class refinement", "data": "synthetic",
+            "config": {"workload": args.workload, "scatterers": len(N),
+                       "N_counts": {str(n): N.count(n) for n in sorted(set(N))}, "n_dir": W["n_dir"],
+                       "k_range": [round(min(ks), 3), round(max(ks), 3)], "parallelism": f"replicas{ws}",
+                       "tile_shape": {"warps": prob.tuning.warps, "ctas_per_sm": prob.tuning.ctas_per_sm,
+                                      "tuned_ms": round(prob.tuning.tuned_ms, 3)},
+                       "l2": "inputs larger than L2 (the 64 matrices are 16.4 GB)"},
+            "scatterers_per_s": round(len(N) / (ms * 1e-3), 2),
+            "efie_entries_per_s": round(sum(n * n for n in N) / (t_asm * 1e-3), 1) if t_asm > 0 else None,
+            "ir_backward_error_max": max(prob.berr), "refinement_iters_max": max(prob.iters),
+            "roofline": roofline, "roofline_calls": calls, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+            "peaks_microbench_tflops": upeaks}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batched(W)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_batched_e2e(args, W):
+    """The batched step through the public API from host arrays: mesh upload of all
+    scatterers, assembly, factorisations and solves, and the download of every solution."""
+    import torch
+
+    from paper_2308_01457_gb300.batched import BatchedProblem
+
+    _, meshes, ks, d, p = _batched_inputs(W)
+    h2d = sum(m.verts.size * 8 + m.tris.size * 4 + m.vnormals.size * 8 for m in meshes)
+    times = []
+    for i in range(max(1, min(args.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        prob = BatchedProblem(meshes, ks, d, p).setup()
+        prob.run(tune=True)
+        host = [x.cpu() for x in prob.X]
+        torch.cuda.synchronize()
+        if i > 0:
+            times.append(time.perf_counter() - t)
+        d2h = sum(x.numel() * 16 for x in host)
+        del prob
+    return {"value": round(statistics.median(times), 4), "unit": "s per batch step", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": len(times)}
+
+
+def cpu_baseline_batched(W):
+    """The FP64 CPU oracle, as it stands, on the batched workload: assembly, plane-wave
+    right-hand sides and the LAPACK solve of all 16 directions, measured for every
+    scatterer with N = 480 and N = 1920 and for the first with N = 7680; each further
+    N = 7680 scatterer is counted at that measured time (the oracle's cost depends on N,
+    not on k or the semi-axes)."""
+    import oracle as O
+
+    O.build()
+    table, meshes, ks, d, p = _batched_inputs(W)
+    t_begin = time.perf_counter()
+    measured, large = 0.0, None
+    n_large = 0
+    for sm, k in zip(meshes, ks):
+        om = O.from_synth(sm)
+        if om.n_edges >= 7680:
+            n_large += 1
+            if large is not None:
+                continue
+        t = time.perf_counter()
+        O.solve(O.assemble_z(om, k), O.rhs_planewave(om, k, d, p))
+        dt = time.perf_counter() - t
+        if om.n_edges >= 7680:
+            large = dt
+        else:
+            measured += dt
+    value = measured + (large or 0.0) * n_large
+    return {"value": round(value, 2), "unit": "s per batch step", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": f"oracle assembly + RHS + LAPACK solve (16 directions) measured for the {64 - n_large} "
+                      f"scatterers with N <= 1920 and one of the {n_large} with N = 7680 ({large:.1f} s), the others "
+                      f"counted at that time; sample {time.perf_counter() - t_begin:.1f} s"}
+
+
 def run_fp64_compare(W, meshes, dirs, out_mixed, ms_mixed):
     """One step of the same workload in plain FP64 (FP64 assembly, complex128 LU on the
     FP64 tensor path, no refinement), outside the timed region: its time, assembly rate
@@ -561,6 +733,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_batched(args):
+    """Reference arm of the batched workload: the FP64 CPU oracle (cpu_baseline_batched) per
+    step; rank 0 only."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        cpu_baseline_batched(W)
+    vals = []
+    for _ in range(args.steps):
+        r = cpu_baseline_batched(W)
+        vals.append(r["value"])
+    v = round(statistics.median(vals), 2)
+    r["value"] = v
+    print(json.dumps({"metric": METRIC, "value": v, "unit": "s per batch step", "n_gpus": ws, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "impl": "reference", "config": {"workload": args.workload, "parallelism": "host cores"},
+                      "cpu_baseline": r,
+                      "e2e": {"value": v, "unit": "s per batch step", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,10 +771,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    batched = WORKLOADS[args.workload].get("kind") == "batched"
     if args.impl == "reference":
-        run_reference(args)
+        run_reference_batched(args) if batched else run_reference(args)
     else:
-        run_fosb(args)
+        run_batched(args) if batched else run_fosb(args)
 
 
 if __name__ == "__main__":

@@ -302,6 +302,50 @@ fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb
                                 int64_t n_inc, const void* U, int64_t ldu, const double* weights, int db, double* sigma,
                                 double* grad, void* stream);
 
+/* ---- Batched scatterers -------------------------------------------------------------
+ * Many independent scatterers of uneven size, each its own EFIE system Z_i u_i = b_i
+ * (Sections II-C and IV-A), processed together: the paper solves its independent
+ * sub-systems concurrently (Section V-D); here the units are whole scatterers. */
+typedef struct {
+  int warps;        /* test triangles per regular-pair tile of the persistent launch (4 or 8) */
+  int ctas_per_sm;  /* resident CTAs per SM of that launch (0: the occupancy limit) */
+  double tuned_ms;  /* the chosen shape's time when the autotuner measured it, else 0 */
+} fosb_batch_tuning;
+
+/* Assembles Z_i (N_i x N_i complex128, ldz[i]) and, where n_inc[i] > 0, b_i (N_i x n_inc[i],
+ * ldb[i]) for every item, as fosb_assemble_efie with prec = FOSB_MIXED would: regular pairs
+ * in float-float (opts->arith = FOSB_ASM_FF, the default here) or FP64 (FOSB_ASM_FP64),
+ * Sauter-Schwab touching pairs in FP64.  With float-float, the regular pairs of all items
+ * run in ONE persistent launch whose CTAs take (item, 32 x W triangle tile) work items
+ * from a device ticket; touching pairs and right-hand sides are one launch each.
+ * tune = 1: the first call for a batch signature (item count, sum of T, sum of T^2) times
+ * each candidate tile shape on this batch and keeps the fastest for later calls in the
+ * process (the batch is then assembled once more with it); chosen (may be NULL) reports
+ * the shape used.
+ *   meshes, k     : host arrays of nbatch handles and wavenumbers
+ *   Z             : host array of nbatch device pointers (caller-owned), ldz host array
+ *   inc, n_inc    : host arrays: inc[i] host n_inc[i] x 9 (d, Re p, Im p); n_inc may be NULL
+ *   b, ldb        : host arrays of device pointers and leading dimensions (used where n_inc[i] > 0)
+ * Enqueued on `stream` (the tuning run synchronises it).  Errors: FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_assemble_efie_batched(int64_t nbatch, const fosb_mesh* meshes, const double* k,
+                                       const fosb_quad_opts* opts, void* const* Z, const int64_t* ldz,
+                                       const double* const* inc, const int64_t* n_inc, void* const* b,
+                                       const int64_t* ldb, int tune, fosb_batch_tuning* chosen, void* stream);
+
+/* Factors and solves every item: X_i = Z_i^{-1} B_i as fosb_factor + fosb_solve with prec
+ * FOSB_MIXED (complex64 factors, FP64 refinement) or FOSB_FP64.  `workers` host threads
+ * (<= 0: 4), each with its own stream, take the items largest first; every item waits for
+ * the work already enqueued on `stream`.  The factorisations are kept until all items are
+ * done and then released (peak memory: every item's factors at once).  stats and
+ * item_status (host arrays of nbatch, may be NULL) receive each item's refinement record and
+ * status.  Returns when all items are done: the first failing item's status, else FOSB_OK.
+ *   Z, B, X : host arrays of device pointers (complex128, row-major), with n, ldz, nrhs,
+ *             ldb, ldx host arrays; X_i may alias B_i. */
+fosb_status fosb_solve_batched(int64_t nbatch, const void* const* Z, const int64_t* n, const int64_t* ldz,
+                               const void* const* B, const int64_t* nrhs, const int64_t* ldb, void* const* X,
+                               const int64_t* ldx, int prec, const fosb_refine_opts* ropt, int workers,
+                               fosb_solve_stats* stats, int* item_status, void* stream);
+
 /* ---- Diagnostics: bounded device waits ---------------------------------------------
  * Every spin-wait of the library's kernels gives up after a number of polls, sets the
  * status word of the call to FOSB_ERR_TIMEOUT and returns, so the call reports

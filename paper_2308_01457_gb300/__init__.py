@@ -44,6 +44,10 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double)]
+
+
 class CovKernel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("ell", ctypes.c_double)]
 
@@ -68,7 +72,8 @@ def lib():
                      "fosb_assemble_efie", "fosb_factor", "fosb_solve", "fosb_lu_info", "fosb_lu_destroy",
                      "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
                      "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read", "fosb_rcs_moments",
-                     "fosb_debug_set_wait_limit", "fosb_peak_microbench"):
+                     "fosb_debug_set_wait_limit", "fosb_peak_microbench", "fosb_assemble_efie_batched",
+                     "fosb_solve_batched"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -271,3 +276,49 @@ def peak_microbench(kind: str) -> float:
     out = ctypes.c_double()
     _check(lib().fosb_peak_microbench(ctypes.c_int(["fp32", "fp64", "tf32", "bf16"].index(kind)), ctypes.byref(out)))
     return out.value
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[None if t is None else t.data_ptr() for t in ts])
+
+
+def _i64_array(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def assemble_efie_batched(meshes, ks, Zs, incs=None, bs=None, n_ss: int = 5, arith: int = ASM_FF, tune: bool = True,
+                          stream=None) -> BatchTuning:
+    """fosb_assemble_efie_batched: Z_i (and b_i for incs[i]) for every scatterer, regular pairs
+    of all of them in one persistent launch.  Returns the tile shape used."""
+    n = len(meshes)
+    opts = QuadOpts(n_ss, arith)
+    handles = (ctypes.c_void_p * n)(*[m.handle.value for m in meshes])
+    kk = (ctypes.c_double * n)(*[float(k) for k in ks])
+    inc_np = [None if incs is None or incs[i] is None else _np(incs[i], np.float64).reshape(-1, 9) for i in range(n)]
+    inc_ptrs = (ctypes.c_void_p * n)(*[None if a is None else a.ctypes.data for a in inc_np])
+    n_inc = _i64_array([0 if a is None else a.shape[0] for a in inc_np])
+    b_list = [None] * n if bs is None else list(bs)
+    tun = BatchTuning()
+    _check(lib().fosb_assemble_efie_batched(ctypes.c_int64(n), handles, kk, ctypes.byref(opts), _ptr_array(Zs),
+                                            _i64_array([_ld(z) for z in Zs]), inc_ptrs, n_inc, _ptr_array(b_list),
+                                            _i64_array([0 if b is None else _ld(b) for b in b_list]),
+                                            ctypes.c_int(int(tune)), ctypes.byref(tun), _stream(stream)))
+    return tun
+
+
+def solve_batched(Zs, Bs, Xs, prec: int = MIXED, workers: int = 4, max_iters: int = 10, tol: float = 0.0,
+                  stream=None):
+    """fosb_solve_batched: X_i = Z_i^{-1} B_i for every item (worker threads take the items
+    largest first).  Returns (iters, backward_error, status) lists."""
+    n = len(Zs)
+    ro = RefineOpts(max_iters, tol)
+    stats = (SolveStats * n)()
+    st = (ctypes.c_int * n)()
+    status = lib().fosb_solve_batched(ctypes.c_int64(n), _ptr_array(Zs), _i64_array([z.shape[0] for z in Zs]),
+                                      _i64_array([_ld(z) for z in Zs]), _ptr_array(Bs),
+                                      _i64_array([1 if b.dim() == 1 else b.shape[1] for b in Bs]),
+                                      _i64_array([_ld(b) for b in Bs]), _ptr_array(Xs),
+                                      _i64_array([_ld(x) for x in Xs]), ctypes.c_int(prec), ctypes.byref(ro),
+                                      ctypes.c_int(workers), stats, st, _stream(stream))
+    _check(status)
+    return [s.iters for s in stats], [s.backward_error for s in stats], list(st)

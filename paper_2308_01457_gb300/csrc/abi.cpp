@@ -12,21 +12,6 @@ using namespace fosb;
 
 namespace {
 
-// Stream-ordered scratch buffer released at scope exit.
-struct Scratch {
-  void* p = nullptr;
-  cudaStream_t s = nullptr;
-  explicit Scratch(cudaStream_t st) : s(st) {}
-  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, std::max<size_t>(bytes, 16), s); }
-  ~Scratch() {
-    if (p) cudaFreeAsync(p, s);
-  }
-  template <typename T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
-
 int g_rules_nss[64];  // per device: the n_ss whose rules are in constant memory (0 = none)
 
 fosb_status ensure_rules(int nss) {
@@ -144,6 +129,8 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
 }
 
 }  // namespace
+
+fosb_status fosb::ensure_rules_for(int nss) { return ensure_rules(nss); }
 
 extern "C" {
 

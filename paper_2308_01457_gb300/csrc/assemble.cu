@@ -15,6 +15,8 @@
 // pairs are skipped here and handled by the Sauter-Schwab kernel.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include <cstdio>
 
 #include "fosb_internal.h"
@@ -231,9 +233,11 @@ __device__ __forceinline__ void ss_accumulate(double k, const double x[3], const
   acc[15] += gi * xy;
 }
 
+// One touching pair (index pair of m.touch) by one 128-thread CTA: Sauter-Schwab moments,
+// block reduction, and the 3 x 3 RWG block added into Z.
 template <typename OutT>
-__global__ void __launch_bounds__(128) efie_singular_kernel(DevMesh m, double k, int nss, OutT* Z, int64_t ldz) {
-  const TouchPair tp = m.touch[blockIdx.x];
+__device__ __forceinline__ void singular_pair(const DevMesh& m, double k, int nss, OutT* Z, int64_t ldz, int64_t pair) {
+  const TouchPair tp = m.touch[pair];
   double P[3][3], Q[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -327,13 +331,48 @@ __global__ void __launch_bounds__(128) efie_singular_kernel(DevMesh m, double k,
   scatter_block(k, mom, p, q, c1, d1, c2, d2, e1, e2, Z, ldz, t1 != t2);
 }
 
+template <typename OutT>
+__global__ void __launch_bounds__(128) efie_singular_kernel(DevMesh m, double k, int nss, OutT* Z, int64_t ldz) {
+  singular_pair(m, k, nss, Z, ldz, blockIdx.x);
+}
+
+// Batched forms over many meshes: a flat grid whose block (singular) or thread (RHS) index
+// falls in the item with the largest start <= index.
+struct BatchItem {
+  DevMesh m;
+  double k;
+  double* Z;
+  int64_t ldz;
+  double* b;
+  int64_t ldb;
+  const double* inc;  // n_inc x 9
+  int64_t n_inc;
+  int64_t pair_start;  // first touching pair of this item in the batch
+  int64_t rhs_start;   // first (triangle, incidence) of this item in the batch
+};
+
+__device__ __forceinline__ int batch_find(const BatchItem* items, int n, int64_t w, bool rhs) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((rhs ? items[mid].rhs_start : items[mid].pair_start) <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) efie_singular_batched_kernel(const BatchItem* __restrict__ items, int nitems,
+                                                                    int nss) {
+  const int i = batch_find(items, nitems, blockIdx.x, false);
+  const BatchItem& it = items[i];
+  singular_pair(it.m, it.k, nss, it.Z, it.ldz, int64_t(blockIdx.x) - it.pair_start);
+}
+
 // ------------------------------------------------------------------ right-hand side
 // b[m, s] = -int E_inc_s . f_m, one thread per (triangle, incidence).
 template <typename OutT>
-__global__ void rhs_kernel(DevMesh m, double k, const double* inc, int64_t n_inc, OutT* b, int64_t ldb) {
-  int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gid >= m.nt * n_inc) return;
-  int64_t t = gid / n_inc, s = gid % n_inc;
+__device__ __forceinline__ void rhs_one(const DevMesh& m, double k, const double* inc, int64_t n_inc, OutT* b,
+                                        int64_t ldb, int64_t t, int64_t s) {
   const double* c = inc + 9 * s;
   double acc_r[3] = {0, 0, 0}, acc_i[3] = {0, 0, 0};
   for (int qp = 0; qp < 6; ++qp) {
@@ -354,6 +393,21 @@ __global__ void rhs_kernel(DevMesh m, double k, const double* inc, int64_t n_inc
   double A = m.tri_area[t];
   for (int i = 0; i < 3; ++i)
     atomic_add_c(b + 2 * (int64_t(m.tri_edge[3 * t + i]) * ldb + s), -A * acc_r[i], -A * acc_i[i]);
+}
+
+template <typename OutT>
+__global__ void rhs_kernel(DevMesh m, double k, const double* inc, int64_t n_inc, OutT* b, int64_t ldb) {
+  int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= m.nt * n_inc) return;
+  rhs_one(m, k, inc, n_inc, b, ldb, gid / n_inc, gid % n_inc);
+}
+
+__global__ void rhs_batched_kernel(const BatchItem* __restrict__ items, int nitems, int64_t total) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const BatchItem& it = items[batch_find(items, nitems, gid, true)];
+  const int64_t local = gid - it.rhs_start;
+  rhs_one(it.m, it.k, it.inc, it.n_inc, it.b, it.ldb, local / it.n_inc, local % it.n_inc);
 }
 
 // ------------------------------------------------------------------ far-field matrix
@@ -563,6 +617,49 @@ cudaError_t launch_bk_product(const DevMesh& m1, const double* B1_ell, const Dev
   else
     bk_product_kernel<double><<<grid, 128, 0, s>>>(m1, B1_ell, m2, ker.kind, ker.sigma, ker.ell, static_cast<double*>(W), ldw);
   return launched();
+}
+
+size_t batched_items_bytes(int nmesh) { return sizeof(BatchItem) * size_t(nmesh); }
+
+// Singular pairs and plane-wave right-hand sides of a batch of meshes (complex128 Z and b,
+// zeroed by the caller), one launch each; d_items: batched_items_bytes(nmesh) bytes of
+// device scratch, inc[i]: device n_inc[i] x 9 (may be NULL when n_inc[i] = 0).
+cudaError_t launch_singular_rhs_batched(const DevMesh* const* meshes, const double* ks, double* const* Z,
+                                        const int64_t* ldz, double* const* b, const int64_t* ldb,
+                                        const double* const* inc, const int64_t* n_inc, int nmesh, int nss,
+                                        void* d_items, cudaStream_t s) {
+  std::vector<BatchItem> items(nmesh);
+  int64_t pairs = 0, rhs = 0;
+  for (int i = 0; i < nmesh; ++i) {
+    BatchItem& it = items[i];
+    it.m = *meshes[i];
+    it.k = ks[i];
+    it.Z = Z[i];
+    it.ldz = ldz[i];
+    it.b = b[i];
+    it.ldb = ldb[i];
+    it.inc = inc[i];
+    it.n_inc = n_inc[i];
+    it.pair_start = pairs;
+    it.rhs_start = rhs;
+    pairs += it.m.ntouch;
+    rhs += it.n_inc > 0 && it.b ? it.m.nt * it.n_inc : 0;
+  }
+  if (pairs > 0x7fffffff) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * nmesh, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const BatchItem* di = static_cast<const BatchItem*>(d_items);
+  if (pairs > 0) {
+    ProfScope prof("asm_singular", s, double(pairs));
+    efie_singular_batched_kernel<<<unsigned(pairs), 128, 0, s>>>(di, nmesh, nss);
+    e = launched();
+    if (e != cudaSuccess) return e;
+  }
+  if (rhs > 0) {
+    rhs_batched_kernel<<<blocks_for(rhs, 128), 128, 0, s>>>(di, nmesh, rhs);
+    e = launched();
+  }
+  return e;
 }
 
 }  // namespace fosb

@@ -19,7 +19,9 @@
 // which is formed in float-float and added to the complex128 Z with FP64 atomics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "fosb_internal.h"
 
@@ -128,14 +130,11 @@ __device__ __forceinline__ void expi_ff(ff theta, const FFConst& C, const float 
   cs = ff_add(ff_mul(Cc, cd), ff_neg(ff_mul(S, sd)));
 }
 
-__global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst C, double* Z, int64_t ldz) {
-  __shared__ float tab[128][4];
-  for (int e = threadIdx.x; e < 128 * 4; e += blockDim.x) tab[e >> 2][e & 3] = c_sctab[e >> 2][e & 3];
-  __syncthreads();
-  const int64_t t1 = int64_t(blockIdx.y) * 4 + (threadIdx.x >> 5);
-  const int64_t t2 = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
+// One regular point pair block: test triangle t1, trial triangle t2 (t1, t2 < m.nt); adds the
+// 3 x 3 RWG block into Z unless the triangles touch.  tab: the sin/cos table in shared memory.
+__device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst& C, double* Z, int64_t ldz,
+                                                int64_t t1, int64_t t2, const float (*tab)[4]) {
   const int64_t nt = m.nt;
-  if (t1 >= nt || t2 >= nt) return;
   int v1[3], v2[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -281,6 +280,72 @@ __global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst
   }
 }
 
+__global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst C, double* Z, int64_t ldz) {
+  __shared__ float tab[128][4];
+  for (int e = threadIdx.x; e < 128 * 4; e += blockDim.x) tab[e >> 2][e & 3] = c_sctab[e >> 2][e & 3];
+  __syncthreads();
+  const int64_t t1 = int64_t(blockIdx.y) * 4 + (threadIdx.x >> 5);
+  const int64_t t2 = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
+  if (t1 >= m.nt || t2 >= m.nt) return;
+  regular_ff_pair(m, C, Z, ldz, t1, t2, tab);
+}
+
+// Batched form: one persistent launch over the tiles of many meshes.  Tile w of the batch
+// (WARPS test triangles x 32 trial triangles) belongs to the item with the largest
+// tile_start <= w; CTAs take tiles from a device ticket until the batch is exhausted, so
+// meshes of uneven size share the GPU without per-mesh launches.
+struct FFBatchItem {
+  DevMesh m;
+  FFConst C;
+  double* Z;
+  int64_t ldz;
+  int64_t tiles_x;     // ceil(nt / 32)
+  int64_t tile_start;  // first tile of this item in the batch
+};
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 640 / (WARPS * 32)) efie_regular_ff_batched_kernel(const FFBatchItem* __restrict__ items,
+                                                                             int nitems, int64_t total_tiles,
+                                                                             unsigned long long* ticket) {
+  __shared__ float tab[128][4];
+  __shared__ FFBatchItem s_item;
+  __shared__ long long s_tile;
+  __shared__ int s_idx;
+  for (int e = threadIdx.x; e < 128 * 4; e += blockDim.x) tab[e >> 2][e & 3] = c_sctab[e >> 2][e & 3];
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long w = static_cast<long long>(atomicAdd(ticket, 1ull));
+      int lo = 0, hi = nitems - 1;
+      if (w < total_tiles)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (items[mid].tile_start <= w) lo = mid;
+          else hi = mid - 1;
+        }
+      s_tile = w;
+      s_idx = lo;
+    }
+    __syncthreads();
+    const long long w = s_tile;
+    const int idx = s_idx;
+    if (w >= total_tiles) break;
+    if (idx != cur) {  // stage the item's record in shared memory (read by every thread)
+      __syncthreads();
+      const int* src = reinterpret_cast<const int*>(items + idx);
+      int* dst = reinterpret_cast<int*>(&s_item);
+      for (int e = threadIdx.x; e < int(sizeof(FFBatchItem) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
+      cur = idx;
+      __syncthreads();
+    }
+    const int64_t local = w - s_item.tile_start;
+    const int64_t ty = local / s_item.tiles_x, tx = local - ty * s_item.tiles_x;
+    const int64_t t1 = ty * WARPS + (threadIdx.x >> 5), t2 = tx * 32 + (threadIdx.x & 31);
+    if (t1 < s_item.m.nt && t2 < s_item.m.nt) regular_ff_pair(s_item.m, s_item.C, s_item.Z, s_item.ldz, t1, t2, tab);
+    __syncthreads();  // s_tile / s_item are rewritten by the next ticket
+  }
+}
+
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
 void split(double x, float& h, float& l) {
@@ -320,8 +385,8 @@ void upload_rules_ff(const Rules& r) {
 // stays below 1024, which keeps j * c1 and j * c2 exact in FP32.
 double ff_max_phase() { return 48.0; }
 
-cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_t ldz, cudaStream_t s) {
-  if (k * m.diameter >= ff_max_phase()) return cudaErrorInvalidValue;
+namespace {
+FFConst make_ff_const(double k) {
   FFConst C;
   C.k = split_ff(k);
   C.k4 = split_ff(k / 4.0);
@@ -333,10 +398,63 @@ cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_
   C.c2 = truncate_bits(pi64 - double(C.c1), 14);
   C.c3 = float(pi64 - double(C.c1) - double(C.c2));
   C.inv_c = float(64.0 / M_PI);
+  return C;
+}
+}  // namespace
+
+cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_t ldz, cudaStream_t s) {
+  if (k * m.diameter >= ff_max_phase()) return cudaErrorInvalidValue;
+  const FFConst C = make_ff_const(k);
   dim3 grid(cdiv(m.nt, 32), cdiv(m.nt, 4));
   if (grid.y > 65535u) return cudaErrorInvalidValue;
   efie_regular_ff_kernel<<<grid, 128, 0, s>>>(m, C, Z, ldz);
   return launched();
 }
+
+// Regular pairs of a batch of meshes in one persistent launch (see efie_regular_ff_batched_kernel):
+// warps = test triangles per tile (4 or 8), ctas_per_sm = resident CTAs per SM (0: the
+// occupancy limit).  Z[i] must be zeroed; ticket is one device word of scratch.
+cudaError_t launch_efie_regular_ff_batched(const DevMesh* const* meshes, const double* ks, double* const* Z,
+                                           const int64_t* ldz, int nmesh, int warps, int ctas_per_sm,
+                                           void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  if (warps != 4 && warps != 8) return cudaErrorInvalidValue;
+  std::vector<FFBatchItem> items(nmesh);
+  int64_t total = 0;
+  for (int i = 0; i < nmesh; ++i) {
+    const DevMesh& m = *meshes[i];
+    if (ks[i] * m.diameter >= ff_max_phase()) return cudaErrorInvalidValue;
+    items[i].m = m;
+    items[i].C = make_ff_const(ks[i]);
+    items[i].Z = Z[i];
+    items[i].ldz = ldz[i];
+    items[i].tiles_x = (m.nt + 31) / 32;
+    items[i].tile_start = total;
+    total += items[i].tiles_x * ((m.nt + warps - 1) / warps);
+  }
+  const size_t need = 256 + sizeof(FFBatchItem) * size_t(nmesh);
+  if (scratch_bytes < need) return cudaErrorInvalidValue;
+  unsigned long long* ticket = static_cast<unsigned long long*>(scratch);
+  FFBatchItem* d_items = reinterpret_cast<FFBatchItem*>(static_cast<char*>(scratch) + 256);
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, items.data(), sizeof(FFBatchItem) * nmesh, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  double pairs = 0.0;
+  for (int i = 0; i < nmesh; ++i) pairs += 36.0 * double(meshes[i]->nt) * double(meshes[i]->nt);
+  ProfScope prof("asm_regular", s, pairs);
+  if (warps == 4) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, efie_regular_ff_batched_kernel<4>, 128, 0);
+    const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    efie_regular_ff_batched_kernel<4><<<unsigned(nsm * per), 128, 0, s>>>(d_items, nmesh, total, ticket);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, efie_regular_ff_batched_kernel<8>, 256, 0);
+    const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    efie_regular_ff_batched_kernel<8><<<unsigned(nsm * per), 256, 0, s>>>(d_items, nmesh, total, ticket);
+  }
+  return launched();
+}
+size_t regular_ff_batched_scratch_bytes(int nmesh) { return 256 + sizeof(FFBatchItem) * size_t(nmesh); }
 
 }  // namespace fosb

@@ -46,6 +46,23 @@ class ProfScope {
   bool active_ = false;
 };
 
+// Stream-ordered scratch buffer released at scope exit.
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes > 16 ? bytes : size_t(16), s); }
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
 #define FOSB_TRY(call)                    \
   do {                                    \
     fosb_status s_ = (call);              \
@@ -114,6 +131,10 @@ struct fosb_lu_s {
 };
 
 namespace fosb {
+
+// Quadrature rules in the device constant memory of every kernel family, for n_ss points
+// per Sauter-Schwab coordinate (uploaded once per device and n_ss).
+fosb_status ensure_rules_for(int nss);
 
 // ---------------------------------------------------------------- quadrature rules
 struct Rules {
