@@ -308,7 +308,7 @@ fosb_status fosb_rcs_monostatic(fosb_mesh mesh, fosb_lu lu, double k, const fosb
  * sub-systems concurrently (Section V-D); here the units are whole scatterers. */
 typedef struct {
   int warps;        /* test triangles per regular-pair tile of the persistent launch (4 or 8) */
-  int ctas_per_sm;  /* resident CTAs per SM of that launch (0: the occupancy limit) */
+  int ctas_per_sm;  /* CTAs per SM its register allocation is bounded for (4 warps: 5 or 4; 8 warps: 2 or 1) */
   double tuned_ms;  /* the chosen shape's time when the autotuner measured it, else 0 */
 } fosb_batch_tuning;
 

@@ -4,7 +4,7 @@
 // fosb_assemble_efie_batched: the regular pairs of every scatterer in one persistent launch
 // that takes (scatterer, tile) work items from a device ticket, then one launch for all
 // touching pairs and one for all right-hand sides.  The tile shape of the persistent launch
-// (test triangles per tile, resident CTAs per SM) is chosen by an autotuner: the first call
+// (test triangles per tile, CTAs per SM of its register bound) is chosen by an autotuner: the first call
 // for a batch signature with tune = 1 times each candidate on the batch itself and keeps
 // the fastest for the rest of the process.
 //
@@ -30,7 +30,7 @@
 
 namespace fosb {
 cudaError_t launch_efie_regular_ff_batched(const DevMesh* const* meshes, const double* ks, double* const* Z,
-                                           const int64_t* ldz, int nmesh, int warps, int ctas_per_sm,
+                                           const int64_t* ldz, int nmesh, int warps, int min_ctas,
                                            void* scratch, size_t scratch_bytes, cudaStream_t s);
 size_t regular_ff_batched_scratch_bytes(int nmesh);
 size_t batched_items_bytes(int nmesh);
@@ -42,10 +42,12 @@ fosb_status ensure_rules_for(int nss);
 
 namespace {
 
+// tile shape of the persistent regular-pair launch: test triangles per tile (warps) and the
+// CTAs per SM its register allocation is bounded for (more CTAs, fewer registers per thread)
 struct Shape {
-  int warps, ctas_per_sm;
+  int warps, min_ctas;
 };
-constexpr Shape kCandidates[] = {{4, 0}, {4, 2}, {8, 0}, {8, 1}};
+constexpr Shape kCandidates[] = {{4, 5}, {4, 4}, {8, 2}, {8, 1}};
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int64_t, int64_t, int64_t>, std::pair<Shape, double>> g_tuned;
@@ -151,7 +153,7 @@ fosb_status fosb_assemble_efie_batched(int64_t nbatch, const fosb_mesh* meshes, 
       for (const Shape& c : kCandidates) {
         if ((err = zero_all()) != cudaSuccess) break;
         cudaEventRecord(e0, s);
-        err = launch_efie_regular_ff_batched(dm.data(), k, dZ.data(), ldz, n, c.warps, c.ctas_per_sm, base, reg_bytes,
+        err = launch_efie_regular_ff_batched(dm.data(), k, dZ.data(), ldz, n, c.warps, c.min_ctas, base, reg_bytes,
                                              s);
         cudaEventRecord(e1, s);
         if (err != cudaSuccess || (err = cudaEventSynchronize(e1)) != cudaSuccess) break;
@@ -174,7 +176,7 @@ fosb_status fosb_assemble_efie_batched(int64_t nbatch, const fosb_mesh* meshes, 
   for (int i = 0; i < n; ++i)
     if (ninc[i] > 0) FOSB_CUDA(cudaMemset2DAsync(db[i], ldb_v[i] * 16, 0, ninc[i] * 16, dm[i]->ne, s));
   if (arith == FOSB_ASM_FF) {
-    FOSB_CUDA(launch_efie_regular_ff_batched(dm.data(), k, dZ.data(), ldz, n, shape.warps, shape.ctas_per_sm, base,
+    FOSB_CUDA(launch_efie_regular_ff_batched(dm.data(), k, dZ.data(), ldz, n, shape.warps, shape.min_ctas, base,
                                              reg_bytes, s));
   } else {
     for (int i = 0; i < n; ++i) FOSB_CUDA(launch_assemble_regular(*dm[i], k[i], FOSB_ASM_FP64, dZ[i], ldz[i], s));
@@ -183,7 +185,7 @@ fosb_status fosb_assemble_efie_batched(int64_t nbatch, const fosb_mesh* meshes, 
                                         n, nss, base + reg_bytes, s));
   if (chosen) {
     chosen->warps = arith == FOSB_ASM_FF ? shape.warps : 0;
-    chosen->ctas_per_sm = arith == FOSB_ASM_FF ? shape.ctas_per_sm : 0;
+    chosen->ctas_per_sm = arith == FOSB_ASM_FF ? shape.min_ctas : 0;
     chosen->tuned_ms = tuned_ms;
   }
   return FOSB_OK;

@@ -303,8 +303,8 @@ struct FFBatchItem {
   int64_t tile_start;  // first tile of this item in the batch
 };
 
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 640 / (WARPS * 32)) efie_regular_ff_batched_kernel(const FFBatchItem* __restrict__ items,
+template <int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) efie_regular_ff_batched_kernel(const FFBatchItem* __restrict__ items,
                                                                              int nitems, int64_t total_tiles,
                                                                              unsigned long long* ticket) {
   __shared__ float tab[128][4];
@@ -412,12 +412,18 @@ cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_
 }
 
 // Regular pairs of a batch of meshes in one persistent launch (see efie_regular_ff_batched_kernel):
-// warps = test triangles per tile (4 or 8), ctas_per_sm = resident CTAs per SM (0: the
-// occupancy limit).  Z[i] must be zeroed; ticket is one device word of scratch.
+// warps = test triangles per tile (4 or 8), min_ctas = the CTAs per SM the register
+// allocation is bounded for (4 warps: 5 or 4; 8 warps: 2 or 1); the grid is every resident
+// CTA.  Z[i] must be zeroed; scratch: regular_ff_batched_scratch_bytes(nmesh) device bytes.
 cudaError_t launch_efie_regular_ff_batched(const DevMesh* const* meshes, const double* ks, double* const* Z,
-                                           const int64_t* ldz, int nmesh, int warps, int ctas_per_sm,
+                                           const int64_t* ldz, int nmesh, int warps, int min_ctas,
                                            void* scratch, size_t scratch_bytes, cudaStream_t s) {
-  if (warps != 4 && warps != 8) return cudaErrorInvalidValue;
+  void (*kern)(const FFBatchItem*, int, int64_t, unsigned long long*) = nullptr;
+  if (warps == 4 && min_ctas == 5) kern = efie_regular_ff_batched_kernel<4, 5>;
+  else if (warps == 4 && min_ctas == 4) kern = efie_regular_ff_batched_kernel<4, 4>;
+  else if (warps == 8 && min_ctas == 2) kern = efie_regular_ff_batched_kernel<8, 2>;
+  else if (warps == 8 && min_ctas == 1) kern = efie_regular_ff_batched_kernel<8, 1>;
+  if (!kern) return cudaErrorInvalidValue;
   std::vector<FFBatchItem> items(nmesh);
   int64_t total = 0;
   for (int i = 0; i < nmesh; ++i) {
@@ -441,18 +447,11 @@ cudaError_t launch_efie_regular_ff_batched(const DevMesh* const* meshes, const d
   int dev = 0, nsm = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, 0);
   double pairs = 0.0;
   for (int i = 0; i < nmesh; ++i) pairs += 36.0 * double(meshes[i]->nt) * double(meshes[i]->nt);
   ProfScope prof("asm_regular", s, pairs);
-  if (warps == 4) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, efie_regular_ff_batched_kernel<4>, 128, 0);
-    const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
-    efie_regular_ff_batched_kernel<4><<<unsigned(nsm * per), 128, 0, s>>>(d_items, nmesh, total, ticket);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, efie_regular_ff_batched_kernel<8>, 256, 0);
-    const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
-    efie_regular_ff_batched_kernel<8><<<unsigned(nsm * per), 256, 0, s>>>(d_items, nmesh, total, ticket);
-  }
+  kern<<<unsigned(nsm * std::max(occ, 1)), warps * 32, 0, s>>>(d_items, nmesh, total, ticket);
   return launched();
 }
 size_t regular_ff_batched_scratch_bytes(int nmesh) { return 256 + sizeof(FFBatchItem) * size_t(nmesh); }
