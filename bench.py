@@ -181,33 +181,41 @@ def run_fosb(args):
         prob.run()
         prob.release()
     barrier()
-    timers = {}
     launches0 = F.lib().fosb_kernel_launches()
     clocks = _clock_sampler(local) if rank == 0 else None
+    # the timed region: K steps and one event per step boundary, nothing else recorded
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record()
+    for i in range(args.steps):
+        out = prob.run()
+        prob.release()
+        ev[i + 1].record()
+    barrier()
+    clk = _clock_summary(clocks)
+    launches = int(F.lib().fosb_kernel_launches() - launches0)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, ws, "cuda")
+    # after it, a profiled pass of two steps: per-phase and per-kernel-family CUDA events
+    import ctypes
+
     families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "trsm_update",
                 "oz_prep", "getrs"]
     for fam in families:  # clear earlier records
         F.lib().fosb_profile_read(fam.encode(), None, None, None)
+    timers = {}
+    prof_steps = 2
     F.lib().fosb_profile_enable(1)
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_start.record()
-    for _ in range(args.steps):
-        out = prob.run(timers)
+    for _ in range(prof_steps):
+        prob.run(timers)
         prob.release()
-    t_end.record()
-    barrier()
+    torch.cuda.synchronize()
     F.lib().fosb_profile_enable(0)
-    clk = _clock_summary(clocks)
-    launches = int(F.lib().fosb_kernel_launches() - launches0)
-    import ctypes
-
     fam_stats = {}
     for fam in families:
         ms_c, n_c, w_c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
         F.lib().fosb_profile_read(fam.encode(), ctypes.byref(ms_c), ctypes.byref(n_c), ctypes.byref(w_c))
-        fam_stats[fam] = {"ms_per_step": ms_c.value / args.steps, "launches_per_step": n_c.value / args.steps,
-                          "work_per_step": w_c.value / args.steps}
-    ms = _max_over_ranks(t_start.elapsed_time(t_end) / args.steps, ws, "cuda")
+        fam_stats[fam] = {"ms_per_step": ms_c.value / prof_steps, "launches_per_step": n_c.value / prof_steps,
+                          "work_per_step": w_c.value / prof_steps}
 
     def avg(name):
         v = timers.get(name, [])
@@ -294,7 +302,9 @@ def run_fosb(args):
         "config": {"workload": args.workload, "levels": W["levels"], "N_levels": [N[l] for l in sorted(N)],
                    "triangles_finest": T, "k": W["k"], "n_dir": W["n_dir"], "ct": [W["L0"], W["L"]],
                    "assembly": args.arith, "parallelism": f"replicas{ws}",
-                   "l2": "inputs larger than L2 (Z at N=30720 is 15 GB)"},
+                   "l2": "inputs larger than L2 (Z at N=30720 is 15 GB)",
+                   "profiling": "phase and kernel-family events from a separate 2-step pass after the timed region"},
+        "median_step_ms": round(statistics.median(step_ms), 2),
         "efie_entries_per_s": round(NL * NL / (t_asm * 1e-3), 1),
         "phase_ms": {"assemble_finest": round(t_asm, 2), "factor_finest": round(t_fac, 2),
                      "solve_finest": round(t_sol, 2), "covariance_ct": round(t_cov, 2)},
@@ -357,7 +367,7 @@ def run_batched(args):
     W = WORKLOADS[args.workload]
     upeaks = {kd: round(F.peak_microbench(kd), 2) for kd in ("fp32", "fp64", "tf32", "bf16")}
     table, meshes, ks, d, p = _batched_inputs(W)
-    prob = BatchedProblem(meshes, ks, d, p).setup()
+    prob = BatchedProblem(meshes, ks, d, p, workers=args.workers).setup()
 
     def barrier():
         torch.cuda.synchronize()
@@ -367,27 +377,32 @@ def run_batched(args):
     for _ in range(args.warmup):  # the first warm-up step runs the autotuner
         prob.run(tune=True)
     barrier()
-    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "oz_prep", "getrs"]
-    for fam in families:
-        F.lib().fosb_profile_read(fam.encode(), None, None, None)
     launches0 = F.lib().fosb_kernel_launches()
     clocks = _clock_sampler(local) if rank == 0 else None
-    F.lib().fosb_profile_enable(1)
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(args.steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record()
+    for i in range(args.steps):
         prob.run(tune=True)
-    t1.record()
+        ev[i + 1].record()
     barrier()
-    F.lib().fosb_profile_enable(0)
     clk = _clock_summary(clocks)
     launches = int(F.lib().fosb_kernel_launches() - launches0)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, ws, "cuda")
+    # kernel-family events from a separate 2-step pass after the timed region
+    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "oz_prep", "getrs"]
+    for f in families:
+        F.lib().fosb_profile_read(f.encode(), None, None, None)
+    F.lib().fosb_profile_enable(1)
+    for _ in range(2):
+        prob.run(tune=True)
+    torch.cuda.synchronize()
+    F.lib().fosb_profile_enable(0)
     fam = {}
     for f in families:
         ms_c, n_c, w_c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
         F.lib().fosb_profile_read(f.encode(), ctypes.byref(ms_c), ctypes.byref(n_c), ctypes.byref(w_c))
-        fam[f] = (ms_c.value / args.steps, n_c.value / args.steps, w_c.value / args.steps)
-    ms = _max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, "cuda")
+        fam[f] = (ms_c.value / 2, n_c.value / 2, w_c.value / 2)
     peaks = _peaks()
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     model = {"lu_update": ("tensor", 1.0, bf16 * TF32_PER_BF16, "cgemm_update_split_kernel"),
@@ -422,6 +437,7 @@ def run_batched(args):
                        "tile_shape": {"warps": prob.tuning.warps, "ctas_per_sm": prob.tuning.ctas_per_sm,
                                       "tuned_ms": round(prob.tuning.tuned_ms, 3)},
                        "l2": "inputs larger than L2 (the 64 matrices are 16.4 GB)"},
+            "median_step_ms": round(statistics.median(step_ms), 2), "solve_workers": args.workers,
             "scatterers_per_s": round(len(N) / (ms * 1e-3), 2),
             "efie_entries_per_s": round(sum(n * n for n in N) / (t_asm * 1e-3), 1) if t_asm > 0 else None,
             "ir_backward_error_max": max(prob.berr), "refinement_iters_max": max(prob.iters),
@@ -447,7 +463,7 @@ def run_batched_e2e(args, W):
     for i in range(max(1, min(args.steps, 3)) + 1):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        prob = BatchedProblem(meshes, ks, d, p).setup()
+        prob = BatchedProblem(meshes, ks, d, p, workers=args.workers).setup()
         prob.run(tune=True)
         host = [x.cpu() for x in prob.X]
         torch.cuda.synchronize()
@@ -769,6 +785,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
+    ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batched solve")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     batched = WORKLOADS[args.workload].get("kind") == "batched"
