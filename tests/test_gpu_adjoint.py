@@ -89,13 +89,13 @@ def test_adjoint_gradient_against_fosb_shape_derivative(F):
         m = F.mesh_create(sm.verts, sm.tris, sm.vnormals)
         N = m.n_edges
         inc = F.incidence(d, p)
-        Z = torch.zeros((N, N), dtype=torch.complex128, device=DEV)
-        B = torch.zeros((N, len(d)), dtype=torch.complex128, device=DEV)
+        Z = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+        B = torch.zeros((N, len(d)), dtype=torch.complex128, device="cuda")
         F.assemble_efie(m, k, Z, inc=inc, b=B)
         lu = F.factor(Z, prec=F.FP64)
         U = torch.zeros_like(B)
         F.solve(lu, B, U)
-        grad = torch.zeros((sm.nv, 3), dtype=torch.float64, device=DEV)
+        grad = torch.zeros((sm.nv, 3), dtype=torch.float64, device="cuda")
         F.rcs_monostatic(m, k, inc, U, lu=lu, weights=w, grad=grad)
         gn = np.sum(grad.cpu().numpy() * sm.vnormals, axis=1)
         om = O.from_synth(sm)
