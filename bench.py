@@ -48,6 +48,10 @@ WORKLOADS = {
     # N = 480 / 1920 / 7680), 16 Fibonacci incident directions each; assembly, complex64 LU
     # with FP64 refinement and the 16 solves of every scatterer
     "batched-ellipsoids-64": dict(kind="batched", n=64, n_dir=16),
+    # Monte Carlo: 512 sample surfaces x_p + xi_p n_p, xi ~ N(0, K) (Gaussian sigma = 0.005,
+    # l = 0.3), of the 1280-triangle sphere (N = 1920), k = 4, d = +z, p = x, 181 H-plane angles
+    "mc-sphere-ka4-N1920-M512": dict(kind="mc", level=3, nsamp=512, k=4.0, sigma=0.005, ell=0.3, n_dir=181,
+                                     d=(0, 0, 1), p=(1, 0, 0), seed=230801457),
 }
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
@@ -475,6 +479,74 @@ def run_batched_e2e(args, W):
             "d2h_bytes_per_step": int(d2h), "steps": len(times)}
 
 
+def run_mc(args):
+    """The Monte Carlo workload: one step = the nominal solve, all sample surfaces (chunks of
+    128: batched assembly and batched factor + solve), their far fields and the sample moments."""
+    import torch
+
+    import fosb_synth as S
+    import paper_2308_01457_gb300 as F
+    from paper_2308_01457_gb300.montecarlo import MonteCarloProblem
+
+    F.build.build()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    sm = S.icosphere(W["level"])
+    dirs = S.hplane_directions(W["n_dir"])
+    z = S.gaussian_field_samples(W["nsamp"], sm.verts.shape[0], seed=W["seed"])
+    prob = MonteCarloProblem(sm, W["k"], W["d"], W["p"], dirs, z, F.COV_GAUSS, W["sigma"], W["ell"], 1.0,
+                             workers=args.workers).setup()
+    for _ in range(args.warmup):
+        out = prob.run()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = F.lib().fosb_kernel_launches()
+    clocks = _clock_sampler(local) if rank == 0 else None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record()
+    for i in range(args.steps):
+        out = prob.run()
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = _clock_summary(clocks)
+    launches = int(F.lib().fosb_kernel_launches() - launches0)
+    ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, ws, "cuda")
+    if rank != 0:
+        return
+    N = prob.base.n_edges
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per Monte Carlo run", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: float-float regular pairs, f64 singular pairs, 3xTF32 LU with FP64-class refinement",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "samples": W["nsamp"], "k": W["k"], "n_dir": W["n_dir"],
+                       "sigma": W["sigma"], "ell": W["ell"], "parallelism": f"replicas{ws}"},
+            "samples_per_s": round(W["nsamp"] / (ms * 1e-3), 1), "gpu_launches": launches, "clocks": clk,
+            "variance_far_field_max": float(np.diag(out[2].cpu().numpy()).real.max())}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        om = O.from_synth(sm)
+        nsub = 8
+        t = time.perf_counter()
+        O.monte_carlo(om, W["k"], W["d"], W["p"], dirs, "gauss", W["sigma"], W["ell"], 1.0, z[:nsub])
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": round(dt / (nsub + 1) * (W["nsamp"] + 1), 2), "unit": "s per Monte Carlo run",
+                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"oracle.monte_carlo on {nsub} of the {W['nsamp']} samples (plus the nominal "
+                                          f"surface) in {dt:.1f} s, counted per surface (every surface costs the same)"}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batched(W):
     """The FP64 CPU oracle, as it stands, on the batched workload: assembly, plane-wave
     right-hand sides and the LAPACK solve of all 16 directions, measured for every
@@ -788,11 +860,19 @@ def main():
     ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batched solve")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
-    batched = WORKLOADS[args.workload].get("kind") == "batched"
+    kind = WORKLOADS[args.workload].get("kind")
     if args.impl == "reference":
-        run_reference_batched(args) if batched else run_reference(args)
+        if kind == "mc":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the default workload; "
+                              "the Monte Carlo workload reports its oracle baseline in its own line"}))
+        else:
+            run_reference_batched(args) if kind == "batched" else run_reference(args)
+    elif kind == "batched":
+        run_batched(args)
+    elif kind == "mc":
+        run_mc(args)
     else:
-        run_batched(args) if batched else run_fosb(args)
+        run_fosb(args)
 
 
 if __name__ == "__main__":

@@ -346,6 +346,34 @@ fosb_status fosb_solve_batched(int64_t nbatch, const void* const* Z, const int64
                                const int64_t* ldx, int prec, const fosb_refine_opts* ropt, int workers,
                                fosb_solve_stats* stats, int* item_status, void* stream);
 
+/* ---- Monte Carlo over random shapes -------------------------------------------------
+ * The paper's reference estimator of the shape statistics (Section V-C): sample surfaces
+ * x_p + t xi_p n_p with xi ~ N(0, K), each solved, and sample moments of the far field.
+ * The samples come from the caller's standard normal draws; the surfaces are solved with
+ * the batched calls above; the moments are formed on the device. */
+
+/* xi_s = L z_s for nsamp draws: K + 1e-12 sigma^2 I = L L^T with K_pq = kernel(|x_p - x_q|)
+ * on the mesh vertices (the random normal velocity expanded at the vertices, Section III).
+ *   z  : host, nsamp x nv standard normal draws;  xi : host, nsamp x nv outputs.
+ * The Cholesky factorisation (nv^3/3 flops) runs on the host in the library.
+ * Errors: FOSB_ERR_INVALID_ARG, FOSB_ERR_SINGULAR (K not positive definite). */
+fosb_status fosb_field_samples(fosb_mesh mesh, const fosb_cov_kernel* kernel, int64_t nsamp, const double* z,
+                               double* xi);
+
+/* The sample surface x_p + t xi_p n_p of base (same triangles, the base's vertex normals n_p)
+ * as a new mesh handle, as fosb_mesh_create would build it.  xi: host, nv values. */
+fosb_status fosb_mesh_perturb(fosb_mesh base, const double* xi, double t, fosb_mesh* out);
+
+/* Sample moments of nsamp far fields.  Fs: device n3 x nsamp complex128 (ldf >= nsamp; column s
+ * the far field F_s of sample s, as a mean-mode fosb_farfield_moments output); F0: device n3,
+ * the nominal far field.  Writes (device, complex128, each may be NULL; pcov needs cov):
+ *   mean = (1/S) sum_s F_s (n3);
+ *   cov  = (1/S) sum_s D_s D_s^H, pcov = (1/S) sum_s D_s D_s^T (n3 x n3, ldc / ldp), D_s = (F_s - F0)/t,
+ * the Monte Carlo counterparts of the first-order Cov[F'] and E[F' F'^T] for perturbation
+ * amplitude t.  Enqueued on `stream`.  Errors: FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_mc_moments(int64_t n3, int64_t nsamp, const void* Fs, int64_t ldf, const void* F0, double t,
+                            void* mean, void* cov, int64_t ldc, void* pcov, int64_t ldp, void* stream);
+
 /* ---- Diagnostics: bounded device waits ---------------------------------------------
  * Every spin-wait of the library's kernels gives up after a number of polls, sets the
  * status word of the call to FOSB_ERR_TIMEOUT and returns, so the call reports

@@ -346,6 +346,26 @@ def rcs_variance_db(F: np.ndarray, cov: np.ndarray, pcov: np.ndarray) -> np.ndar
     return out
 
 
+def monte_carlo(mesh: RWGMesh, k: float, d, p, xhat, kind: str, sigma: float, ell: float, t: float, z):
+    """Monte Carlo estimator of the far-field statistics (Section V-C): sample surfaces
+    x_p + t xi_p n_p with xi = L z, L L^T = K + 1e-12 sigma^2 I (numpy Cholesky; z: nsamp x nv
+    standard normal draws), each assembled and solved with LAPACK.  Returns (F0, the samples
+    F_s (S x 3 n_dir), (1/S) sum D D^H, (1/S) sum D D^T) with D_s = (F_s - F0)/t."""
+    K = cov_kernel(mesh.verts, mesh.verts, kind, sigma, ell) + 1e-12 * sigma**2 * np.eye(mesh.nv)
+    xi = np.asarray(z, dtype=np.float64) @ np.linalg.cholesky(K).T
+
+    def far(verts):
+        m = RWGMesh(verts, mesh.tris, mesh.vnormals)
+        u = solve(assemble_z(m, k), rhs_planewave(m, k, d, p)[:, 0])
+        return farfield_matrix(m, k, xhat) @ u
+
+    F0 = far(mesh.verts)
+    Fs = np.stack([far(mesh.verts + t * x[:, None] * mesh.vnormals) for x in xi])
+    D = (Fs - F0[None]) / t
+    S = Fs.shape[0]
+    return F0, Fs, D.T @ D.conj() / S, D.T @ D / S
+
+
 # ---------------------------------------------------------------------------
 # Shape derivatives of the discrete quantities (forward mode, efie_oracle_grad.cpp)
 # ---------------------------------------------------------------------------

@@ -73,7 +73,7 @@ def lib():
                      "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
                      "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read", "fosb_rcs_moments",
                      "fosb_debug_set_wait_limit", "fosb_peak_microbench", "fosb_assemble_efie_batched",
-                     "fosb_solve_batched"):
+                     "fosb_solve_batched", "fosb_field_samples", "fosb_mesh_perturb", "fosb_mc_moments"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -116,6 +116,15 @@ def _prec_of(t) -> int:
 
 class Mesh:
     """Handle of fosb_mesh_create (RWG tables on the device)."""
+
+    @classmethod
+    def _from_handle(cls, h):
+        self = cls.__new__(cls)
+        self.handle = h
+        nv, nt, ne, ntouch = (ctypes.c_int64() for _ in range(4))
+        _check(lib().fosb_mesh_info(h, ctypes.byref(nv), ctypes.byref(nt), ctypes.byref(ne), ctypes.byref(ntouch)))
+        self.nv, self.nt, self.n_edges, self.n_touching = nv.value, nt.value, ne.value, ntouch.value
+        return self
 
     def __init__(self, verts, tris, vnormals=None):
         v = _np(verts, np.float64)
@@ -322,3 +331,33 @@ def solve_batched(Zs, Bs, Xs, prec: int = MIXED, workers: int = 4, max_iters: in
                                       ctypes.c_int(workers), stats, st, _stream(stream))
     _check(status)
     return [s.iters for s in stats], [s.backward_error for s in stats], list(st)
+
+
+def field_samples(mesh: Mesh, z, kind: int = COV_GAUSS, sigma: float = 1.0, ell: float = 1.0):
+    """fosb_field_samples: xi (nsamp x nv, numpy) = L z with L L^T the vertex covariance."""
+    zz = _np(z, np.float64)
+    xi = np.zeros_like(zz)
+    ker = CovKernel(kind, sigma, ell)
+    _check(lib().fosb_field_samples(mesh.handle, ctypes.byref(ker), ctypes.c_int64(zz.shape[0]),
+                                    zz.ctypes.data_as(ctypes.c_void_p), xi.ctypes.data_as(ctypes.c_void_p)))
+    return xi
+
+
+def mesh_perturb(base: Mesh, xi, t: float) -> Mesh:
+    """fosb_mesh_perturb: the surface x_p + t xi_p n_p of base as a new mesh."""
+    x = _np(xi, np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().fosb_mesh_perturb(base.handle, x.ctypes.data_as(ctypes.c_void_p), ctypes.c_double(t),
+                                   ctypes.byref(h)))
+    return Mesh._from_handle(h)
+
+
+def mc_moments(Fs, F0, t: float, mean=None, cov=None, pcov=None, stream=None):
+    """fosb_mc_moments: sample mean of the columns of Fs and covariance / pseudo-covariance
+    of (F_s - F0)/t, into the given device tensors."""
+    _check(lib().fosb_mc_moments(ctypes.c_int64(Fs.shape[0]), ctypes.c_int64(Fs.shape[1]), _ptr(Fs),
+                                 ctypes.c_int64(_ld(Fs)), _ptr(F0), ctypes.c_double(t),
+                                 None if mean is None else _ptr(mean), None if cov is None else _ptr(cov),
+                                 ctypes.c_int64(0 if cov is None else _ld(cov)), None if pcov is None else _ptr(pcov),
+                                 ctypes.c_int64(0 if pcov is None else _ld(pcov)), _stream(stream)))
+    return mean, cov, pcov

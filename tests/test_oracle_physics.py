@@ -138,9 +138,10 @@ def test_covariance_identities(oracle_mod):
 
 
 def test_monte_carlo_matches_first_order_covariance(oracle_mod):
-    """Perturbed-mesh Monte Carlo (Section V-C) on the 120-edge sphere, xi ~ N(0, K),
-    t xi n_p displacements: the sample covariance of (F_t - F)/t approaches A Sigma A^H
-    within discretisation (about 15% at this level, see the FD pin) and sampling error."""
+    """Perturbed-mesh Monte Carlo (Section V-C, oracle.monte_carlo) on the 120-edge sphere,
+    xi ~ N(0, K), t xi n_p displacements: the sample covariance of (F_t - F)/t approaches
+    A Sigma A^H within discretisation (about 15% at this level, see the FD pin) and sampling
+    error, and the sample variance of RCS_dB over the sample surfaces approaches the delta method."""
     xh = S.hplane_directions(7)
     k, sigma, ell = 2.0, 1.0, 0.5
     sm = S.icosphere(1)
@@ -149,11 +150,10 @@ def test_monte_carlo_matches_first_order_covariance(oracle_mod):
     B = O.sd_rhs(m, k, u)
     K = O.cov_kernel(m.verts, m.verts, "gauss", sigma, ell)
     cov = A @ O.covariance(Z, B, Z, B, K) @ A.conj().T
-    L = np.linalg.cholesky(K + 1e-12 * np.eye(K.shape[0]))
     M, t = 400, 1e-3
-    xis = S.gaussian_field_samples(M, m.nv, seed=7) @ L.T
-    D = np.stack([(_far(sm.verts + t * x[:, None] * sm.vnormals, sm, k, xh)[0] - F0) / t for x in xis])
-    mc = D.T @ D.conj() / M
+    F0m, Fs, mc, mc_p = O.monte_carlo(m, k, [0, 0, 1], [1, 0, 0], xh, "gauss", sigma, ell, t,
+                                      S.gaussian_field_samples(M, m.nv, seed=7))
+    assert np.abs(F0m - F0).max() <= 1e-14 * np.abs(F0).max()
     var_rel = np.linalg.norm(np.diag(mc).real - np.diag(cov).real) / np.linalg.norm(np.diag(cov).real)
     assert var_rel < 0.35, var_rel
     full_rel = np.linalg.norm(mc - cov) / np.linalg.norm(cov)
@@ -162,7 +162,7 @@ def test_monte_carlo_matches_first_order_covariance(oracle_mod):
     # the first-order covariance and pseudo-covariance (the paper's MC-vs-FOSB comparison)
     pcov = A @ O.covariance(Z, B, Z, B, K, pseudo=True) @ A.T
     pred = O.rcs_variance_db(F0.reshape(-1, 3), cov, pcov)
-    rcs = O.rcs_db((F0[None] + t * D).reshape(M, -1, 3))
+    rcs = O.rcs_db(Fs.reshape(M, -1, 3))
     ratio = np.var(rcs, axis=0) / t**2 / pred
     assert np.abs(np.median(ratio) - 1) < 0.25 and np.abs(ratio - 1).max() < 0.6, ratio
 
