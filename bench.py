@@ -857,7 +857,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
-    ap.add_argument("--workers", type=int, default=8, help="host worker threads of the batched solve")
+    ap.add_argument("--workers", type=int, default=4, help="host worker threads of the batched solve")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     kind = WORKLOADS[args.workload].get("kind")
