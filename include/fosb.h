@@ -85,10 +85,20 @@ typedef struct {
   double tol;        /* stop when ||b - Z x||_inf / (||Z||_inf ||x||_inf + ||b||_inf) <= tol per column;
                         tol <= 0 selects the default max(64, 8 sqrt(n)) * 2^-52.  Refinement also stops
                         when a step gains less than a factor 2 below 1e-13 (rounding floor reached) */
+  int solver;        /* FOSB_REFINE_AUTO (0): refinement, then GMRES-IR for the columns it left above tol;
+                        FOSB_REFINE_IR (1): refinement only; FOSB_REFINE_GMRES (2): GMRES-IR from the start */
 } fosb_refine_opts;
 
+/* GMRES-based iterative refinement (the Krylov part of the paper's solver stack, Section IV):
+ * each step solves the correction equation Z d = r (r = b - Z x in FP64-class arithmetic) by
+ * GMRES(50) on M^-1 Z d = M^-1 r, preconditioned by the complex64 factors M, with FP64-class
+ * matrix-vector products and FP64 Arnoldi (two-pass classical Gram-Schmidt); it converges
+ * where plain refinement stalls because kappa(Z) u_32 is not small (Carson and Higham,
+ * SIAM J. Sci. Comput. 40, 2018). */
+enum { FOSB_REFINE_AUTO = 0, FOSB_REFINE_IR = 1, FOSB_REFINE_GMRES = 2 };
+
 typedef struct {
-  int iters;             /* refinement steps taken (0 for FOSB_FP64 / FOSB_FP32) */
+  int iters;             /* refinement steps taken plus GMRES iterations (0 for FOSB_FP64 / FOSB_FP32) */
   double backward_error; /* final normwise relative backward error (max over right-hand sides) */
 } fosb_solve_stats;
 

@@ -19,6 +19,7 @@ from . import build as _build
 FOSB_OK, FOSB_ERR_INVALID_ARG, FOSB_ERR_MESH, FOSB_ERR_SINGULAR, FOSB_ERR_NOT_CONVERGED, FOSB_ERR_OOM, \
     FOSB_ERR_CUDA, FOSB_ERR_TIMEOUT = range(8)
 FP64, MIXED, FP32 = 0, 1, 2
+REFINE_AUTO, REFINE_IR, REFINE_GMRES = 0, 1, 2
 ASM_FP64, ASM_FF, ASM_FP32 = 0, 1, 2
 COV_GAUSS, COV_MATERN32 = 0, 1
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "MESH", 3: "SINGULAR", 4: "NOT_CONVERGED", 5: "OOM", 6: "CUDA", 7: "TIMEOUT"}
@@ -37,7 +38,7 @@ class QuadOpts(ctypes.Structure):
 
 
 class RefineOpts(ctypes.Structure):
-    _fields_ = [("max_iters", ctypes.c_int), ("tol", ctypes.c_double)]
+    _fields_ = [("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("solver", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -196,12 +197,13 @@ def factor(Z, prec: int | None = None, stream=None) -> LU:
     return LU(h, Z.shape[0], prec, Z)
 
 
-def solve(lu: LU, B, X=None, max_iters: int = 10, tol: float = 0.0, stream=None):
-    """fosb_solve: X = Z^{-1} B (in place when X is None).  Returns (X, iters, backward_error)."""
+def solve(lu: LU, B, X=None, max_iters: int = 10, tol: float = 0.0, solver: int = REFINE_AUTO, stream=None):
+    """fosb_solve: X = Z^{-1} B (in place when X is None).  Returns (X, iters, backward_error).
+    solver: REFINE_AUTO (refinement, GMRES-IR where it stalls), REFINE_IR, REFINE_GMRES."""
     X = B if X is None else X
     nrhs = 1 if B.dim() == 1 else B.shape[1]
     st = SolveStats()
-    ro = RefineOpts(max_iters, tol)
+    ro = RefineOpts(max_iters, tol, solver)
     _check(lib().fosb_solve(lu.handle, ctypes.c_char(b"N"), _ptr(B), ctypes.c_int64(nrhs),
                             ctypes.c_int64(1 if B.dim() == 1 else _ld(B)), _ptr(X), ctypes.c_int64(1 if X.dim() == 1 else _ld(X)),
                             ctypes.byref(ro), ctypes.byref(st), _stream(stream)))

@@ -2,6 +2,7 @@
 // (iterative refinement) around the kernels.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -43,6 +44,129 @@ fosb_status col_norms(const void* A, int64_t rows, int64_t cols, int64_t lda, do
   out.resize(cols);
   FOSB_CUDA(cudaMemcpyAsync(out.data(), d_buf, sizeof(double) * cols, cudaMemcpyDeviceToHost, s));
   FOSB_CUDA(cudaStreamSynchronize(s));
+  return FOSB_OK;
+}
+
+// GMRES-based iterative refinement of one column (contiguous device n-vectors bc, xc; see
+// FOSB_REFINE_GMRES in fosb.h): outer steps r = b - Z x (FP64-class), berr test, then the
+// correction d from GMRES on M^-1 Z d = M^-1 r (M the complex64 factors) with FP64 Arnoldi
+// (two-pass classical Gram-Schmidt, complex Givens rotations on the host) and x += d.
+fosb_status gmres_ir_column(fosb_lu lu, const void* bc, void* xc, double bnorm, double tol, int max_outer,
+                            int* iters, double* berr_out, cudaStream_t s) {
+  using cd = std::complex<double>;
+  const int64_t n = lu->n;
+  constexpr int kM = 50;             // Krylov dimension per correction solve
+  constexpr double kInnerTol = 1e-6;  // relative residual of the preconditioned correction equation
+  Scratch V(s), w(s), r(s), hb(s), t32(s), nb(s);
+  FOSB_CUDA(V.alloc(16 * n * (kM + 1)));
+  FOSB_CUDA(w.alloc(16 * n));
+  FOSB_CUDA(r.alloc(16 * n));
+  FOSB_CUDA(hb.alloc(16 * (kM + 2)));
+  FOSB_CUDA(t32.alloc(8 * n));
+  FOSB_CUDA(nb.alloc(sizeof(double) * 2));
+  char* Vp = static_cast<char*>(V.p);
+  const int64_t ldv = kM + 1;
+  auto col = [&](int j) { return static_cast<void*>(Vp + 16 * int64_t(j)); };
+  auto precond = [&](const void* src, void* dst) -> fosb_status {  // dst = M^-1 src
+    FOSB_CUDA(convert_c128_to_c64(src, n, 1, 1, t32.p, 1, s));
+    FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, t32.p, 1, 1, s, lu->d_status, lu->dinv));
+    FOSB_CUDA(convert_c64_to_c128(t32.p, n, 1, 1, dst, 1, s));
+    return FOSB_OK;
+  };
+  // h (k values, host) = V(:, 0:k)^H x
+  auto vdot = [&](int k, const void* x, int64_t incx, std::vector<cd>& h) -> fosb_status {
+    FOSB_CUDA(gemm<double>(OP_C, OP_N, k, 1, n, 1.0, 0.0, V.p, ldv, x, incx, 0.0, hb.p, 1, s));
+    h.resize(k);
+    FOSB_CUDA(cudaMemcpyAsync(h.data(), hb.p, 16 * k, cudaMemcpyDeviceToHost, s));
+    FOSB_CUDA(cudaStreamSynchronize(s));
+    return FOSB_OK;
+  };
+  // ||x||_2 of a device vector with stride incx
+  auto nrm2 = [&](const void* x, int64_t incx, double* out) -> fosb_status {
+    FOSB_CUDA(gemm<double>(OP_C, OP_N, 1, 1, n, 1.0, 0.0, x, incx, x, incx, 0.0, hb.p, 1, s));
+    cd v;
+    FOSB_CUDA(cudaMemcpyAsync(&v, hb.p, 16, cudaMemcpyDeviceToHost, s));
+    FOSB_CUDA(cudaStreamSynchronize(s));
+    *out = std::sqrt(std::max(v.real(), 0.0));
+    return FOSB_OK;
+  };
+  std::vector<double> rn, xn;
+  double berr = INFINITY;
+  int total = 0;
+  for (int outer = 0;; ++outer) {
+    FOSB_CUDA(copy_matrix(bc, n, 1, 1, r.p, 1, 16, s));
+    FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, 1, n, -1.0, 0.0, lu->zref, lu->ldz, xc, 1, 1.0, r.p, 1, s, lu->zff));
+    FOSB_TRY(col_norms(r.p, n, 1, 1, nb.as<double>(), rn, s));
+    FOSB_TRY(col_norms(xc, n, 1, 1, nb.as<double>(), xn, s));
+    const double den = lu->znorm_inf * xn[0] + bnorm;
+    berr = den > 0 ? rn[0] / den : 0.0;
+    if (berr <= tol || outer >= max_outer) break;
+    // GMRES on M^-1 Z d = M^-1 r, d = 0 initially
+    FOSB_TRY(precond(r.p, w.p));
+    double beta = 0.0;
+    FOSB_TRY(nrm2(w.p, 1, &beta));
+    if (!(beta > 0.0)) break;
+    FOSB_CUDA(zscal_copy(n, 1.0 / beta, 0.0, w.p, 1, col(0), ldv, s));
+    std::vector<std::vector<cd>> H;  // column j: H[0..j+1][j], rotated in place
+    std::vector<double> cs;
+    std::vector<cd> sn, g(1, cd(beta, 0.0)), h, h2;
+    int jm = 0;
+    for (int j = 0; j < kM; ++j) {
+      FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, n, 1, n, 1.0, 0.0, lu->zref, lu->ldz, col(j), ldv, 0.0, r.p, 1, s, lu->zff));
+      FOSB_TRY(precond(r.p, w.p));
+      // two passes of classical Gram-Schmidt against v_0 .. v_j
+      FOSB_TRY(vdot(j + 1, w.p, 1, h));
+      FOSB_CUDA(cudaMemcpyAsync(hb.p, h.data(), 16 * (j + 1), cudaMemcpyHostToDevice, s));
+      FOSB_CUDA(gemm<double>(OP_N, OP_N, n, 1, j + 1, -1.0, 0.0, V.p, ldv, hb.p, 1, 1.0, w.p, 1, s));
+      FOSB_TRY(vdot(j + 1, w.p, 1, h2));
+      FOSB_CUDA(cudaMemcpyAsync(hb.p, h2.data(), 16 * (j + 1), cudaMemcpyHostToDevice, s));
+      FOSB_CUDA(gemm<double>(OP_N, OP_N, n, 1, j + 1, -1.0, 0.0, V.p, ldv, hb.p, 1, 1.0, w.p, 1, s));
+      for (int i = 0; i <= j; ++i) h[i] += h2[i];
+      double hn = 0.0;
+      FOSB_TRY(nrm2(w.p, 1, &hn));
+      std::vector<cd> hc(h);
+      hc.push_back(cd(hn, 0.0));
+      for (int i = 0; i < j; ++i) {  // earlier rotations
+        const cd a = hc[i], b = hc[i + 1];
+        hc[i] = cs[i] * a + sn[i] * b;
+        hc[i + 1] = -std::conj(sn[i]) * a + cs[i] * b;
+      }
+      const cd a = hc[j], b = hc[j + 1];
+      double c;
+      cd sv;
+      if (std::abs(a) == 0.0) {
+        c = 0.0;
+        sv = cd(1.0, 0.0);
+      } else {
+        const double nu = std::sqrt(std::norm(a) + std::norm(b));
+        c = std::abs(a) / nu;
+        sv = (a / std::abs(a)) * std::conj(b) / nu;
+      }
+      cs.push_back(c);
+      sn.push_back(sv);
+      hc[j] = c * a + sv * b;
+      hc[j + 1] = 0.0;
+      g.push_back(-std::conj(sv) * g[j]);
+      g[j] = c * g[j];
+      H.push_back(hc);
+      jm = j + 1;
+      ++total;
+      if (std::abs(g[j + 1]) <= kInnerTol * beta || !(hn > 0.0)) break;
+      FOSB_CUDA(zscal_copy(n, 1.0 / hn, 0.0, w.p, 1, col(j + 1), ldv, s));
+    }
+    // y = R^-1 g (R upper triangular jm x jm), d = V y, x += d
+    std::vector<cd> y(jm);
+    for (int i = jm - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int k = i + 1; k < jm; ++k) acc -= H[k][i] * y[k];
+      y[i] = H[i][i] == cd(0.0) ? cd(0.0) : acc / H[i][i];
+    }
+    FOSB_CUDA(cudaMemcpyAsync(hb.p, y.data(), 16 * jm, cudaMemcpyHostToDevice, s));
+    FOSB_CUDA(gemm<double>(OP_N, OP_N, n, 1, jm, 1.0, 0.0, V.p, ldv, hb.p, 1, 1.0, xc, 1, s));
+    FOSB_CUDA(cudaStreamSynchronize(s));  // y is released at the end of this step
+  }
+  *iters += total;
+  *berr_out = berr;
   return FOSB_OK;
 }
 
@@ -88,9 +212,12 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
   FOSB_CUDA(convert_c128_to_c64(Bsrc, n, nrhs, ldbs, d.p, nrhs, s));
   FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status, lu->dinv));
   FOSB_CUDA(convert_c64_to_c128(d.p, n, nrhs, nrhs, X, ldx, s));
+  const int solver = ropt ? ropt->solver : FOSB_REFINE_AUTO;
+  if (solver < FOSB_REFINE_AUTO || solver > FOSB_REFINE_GMRES)
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_solve: unknown refinement solver");
   double prev = INFINITY, prev2 = INFINITY, berr = INFINITY;
   int it = 0;
-  for (;;) {
+  for (; solver != FOSB_REFINE_GMRES;) {
     FOSB_CUDA(copy_matrix(Bsrc, n, nrhs, ldbs, r.p, nrhs, 16, s));
     if (lu->zdig && nrhs > 4)  // 5 or more right-hand sides: digit-split bf16 tensor cores
       FOSB_CUDA(oz_gemm(n, nrhs, n, -1.0, 0.0, lu->zdig, lu->zex, X, ldx, 1.0, r.p, nrhs, lu->d_status, s));
@@ -113,6 +240,24 @@ fosb_status solve_internal(fosb_lu lu, const void* B, int64_t nrhs, int64_t ldb,
     FOSB_CUDA(getrs<float>(lu->lu, n, n, lu->ipiv, d.p, nrhs, nrhs, s, lu->d_status, lu->dinv));
     FOSB_CUDA(axpy_c64_into_c128(d.p, n, nrhs, nrhs, X, ldx, s));
     ++it;
+  }
+  if (solver == FOSB_REFINE_GMRES || (solver == FOSB_REFINE_AUTO && !(berr <= tol) && !(berr <= 1e-13))) {
+    // GMRES-IR column by column for the columns refinement left above the tolerance
+    Scratch xc(s);
+    FOSB_CUDA(xc.alloc(16 * n));
+    berr = 0.0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      const char* bcol = static_cast<const char*>(Bsrc) + 16 * c;
+      char* xcol = static_cast<char*>(X) + 16 * c;
+      Scratch bcs(s);
+      FOSB_CUDA(bcs.alloc(16 * n));
+      FOSB_CUDA(copy_matrix(bcol, n, 1, ldbs, bcs.p, 1, 16, s));
+      FOSB_CUDA(copy_matrix(xcol, n, 1, ldx, xc.p, 1, 16, s));
+      double bc_err = 0.0;
+      FOSB_TRY(gmres_ir_column(lu, bcs.p, xc.p, bn[c], tol, max_iters, &it, &bc_err, s));
+      FOSB_CUDA(copy_matrix(xc.p, n, 1, 1, xcol, ldx, 16, s));
+      berr = std::max(berr, bc_err);
+    }
   }
   if (stats) {
     stats->iters = it;

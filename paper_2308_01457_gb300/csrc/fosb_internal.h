@@ -247,6 +247,10 @@ cudaError_t axpy_c64_into_c128(const void* d, int64_t rows, int64_t cols, int64_
 // out = (accumulate ? out : 0) + w (M + op(M)) for a square n x n matrix M (op = OP_T or OP_C)
 cudaError_t add_mirrored(const void* M, int64_t n, int64_t ldm, int op, double w, bool accumulate, bool c64, void* out,
                          int64_t ldo, cudaStream_t s);
+// complex128 vectors (strides in elements): y = alpha x, y += alpha x (krylov.cu)
+cudaError_t zscal_copy(int64_t n, double ar, double ai, const void* x, int64_t incx, void* y, int64_t incy,
+                       cudaStream_t s);
+cudaError_t zaxpy(int64_t n, double ar, double ai, const void* x, int64_t incx, void* y, int64_t incy, cudaStream_t s);
 // Poll limits of the bounded device waits on the current device (polls <= 0: default):
 // panel grid barriers (linalg.cu) and streaming-sweep flags (trsv_stream.cu).
 cudaError_t set_wait_limit_panels(long long polls);
