@@ -206,19 +206,65 @@ __global__ void __launch_bounds__(256) efie_regular_kernel(DevMesh m, double k, 
 // ------------------------------------------------------------------ singular pairs
 // One CTA of 128 threads per touching pair; the Sauter-Schwab 4-cube points are split
 // over the threads, the moments reduced through shared memory.  FP64 throughout.
-__device__ __forceinline__ void chi_rel(const double P[3][3], double u1, double u2, double out[3]) {
-  // chi(u) - P0 = u1 (P1 - P0) + u2 (P2 - P1)
+// chi(u) - P0 = u1 (P1 - P0) + u2 (P2 - P1), with the edge vectors E[0] = P1 - P0 and
+// E[1] = P2 - P1 formed once per pair
+__device__ __forceinline__ void chi_rel(const double E[2][3], double u1, double u2, double out[3]) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) out[c] = u1 * (P[1][c] - P[0][c]) + u2 * (P[2][c] - P[1][c]);
+  for (int c = 0; c < 3; ++c) out[c] = fma(u1, E[0][c], u2 * E[1][c]);
+}
+
+// exp(i th) for 0 <= th <= 64 in FP64: Cody-Waite reduction th = n pi/2 + d (pi/2 split in
+// three parts, the first with 33 significant bits so that n times it is exact), |d| <= pi/4,
+// and the Taylor series of sin d / d to d^16 and of cos d to d^18 (truncation below 2e-20
+// relative), then the quadrant n mod 4.  Larger phases, which no touching pair of a resolved
+// mesh reaches, fall back to sincos.
+__device__ __forceinline__ void ss_expi(double th, double& c, double& s) {
+  if (!(th <= 64.0)) {
+    sincos(th, &s, &c);
+    return;
+  }
+  const double n = rint(th * 0.6366197723675814);
+  const double d = fma(-n, 3.5215598651832e-27, fma(-n, 6.077100506506192e-11, fma(-n, 1.5707963267341256, th)));
+  const double d2 = d * d;
+  // sin d / d = sum_i (-d2)^i / (2i + 1)!,  cos d = sum_i (-d2)^i / (2i)!
+  double ps = 1.0 / 355687428096000.0;          // 1/17!
+  ps = fma(ps, -d2, 1.0 / 1307674368000.0);     // 1/15!
+  ps = fma(ps, -d2, 1.0 / 6227020800.0);        // 1/13!
+  ps = fma(ps, -d2, 1.0 / 39916800.0);          // 1/11!
+  ps = fma(ps, -d2, 1.0 / 362880.0);            // 1/9!
+  ps = fma(ps, -d2, 1.0 / 5040.0);              // 1/7!
+  ps = fma(ps, -d2, 1.0 / 120.0);               // 1/5!
+  ps = fma(ps, -d2, 1.0 / 6.0);                 // 1/3!
+  ps = fma(ps, -d2, 1.0);
+  double pc = 1.0 / 6402373705728000.0;         // 1/18!
+  pc = fma(pc, -d2, 1.0 / 20922789888000.0);    // 1/16!
+  pc = fma(pc, -d2, 1.0 / 87178291200.0);       // 1/14!
+  pc = fma(pc, -d2, 1.0 / 479001600.0);         // 1/12!
+  pc = fma(pc, -d2, 1.0 / 3628800.0);           // 1/10!
+  pc = fma(pc, -d2, 1.0 / 40320.0);             // 1/8!
+  pc = fma(pc, -d2, 1.0 / 720.0);               // 1/6!
+  pc = fma(pc, -d2, 1.0 / 24.0);                // 1/4!
+  pc = fma(pc, -d2, 0.5);                       // 1/2!
+  pc = fma(pc, -d2, 1.0);
+  const double sd = d * ps, cd = pc;
+  // sin(d + q pi/2), cos(d + q pi/2) for q = n mod 4
+  const int q = int(n) & 3;
+  s = q == 0 ? sd : (q == 1 ? cd : (q == 2 ? -sd : -cd));
+  c = q == 0 ? cd : (q == 1 ? -sd : (q == 2 ? -cd : sd));
 }
 
 __device__ __forceinline__ void ss_accumulate(double k, const double x[3], const double y[3], double w, double acc[16]) {
-  double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
-  double r = sqrt(dx * dx + dy * dy + dz * dz);
+  const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  // 1/r from a float seed and two Newton steps in FP64, y <- y (3 - r2 y^2) / 2:
+  // about 22, then 44, then full significant bits
+  double yr = double(rsqrtf(float(r2)));
+  yr = yr * fma(-0.5 * r2, yr * yr, 1.5);
+  yr = yr * fma(-0.5 * r2, yr * yr, 1.5);
   double sn, cs;
-  sincos(k * r, &sn, &cs);
-  double g = w / r;
-  double gr = cs * g, gi = sn * g;
+  ss_expi(k * (r2 * yr), cs, sn);
+  const double g = w * yr;
+  const double gr = cs * g, gi = sn * g;
   acc[0] += gr;
   acc[1] += gi;
 #pragma unroll
@@ -233,10 +279,13 @@ __device__ __forceinline__ void ss_accumulate(double k, const double x[3], const
   acc[15] += gi * xy;
 }
 
-// One touching pair (index pair of m.touch) by one 128-thread CTA: Sauter-Schwab moments,
-// block reduction, and the 3 x 3 RWG block added into Z.
+// One touching pair (index pair of m.touch) by one warp: the lanes share the Sauter-Schwab
+// 4-cube points, a butterfly reduction leaves the 16 moments in every lane, and lanes 0-8
+// form one entry each of the 3 x 3 RWG block and add it (and its mirror) into Z.
 template <typename OutT>
 __device__ __forceinline__ void singular_pair(const DevMesh& m, double k, int nss, OutT* Z, int64_t ldz, int64_t pair) {
+  const int lane = threadIdx.x & 31;
+  const double kinv = 1.0 / k;
   const TouchPair tp = m.touch[pair];
   double P[3][3], Q[3][3];
 #pragma unroll
@@ -247,11 +296,19 @@ __device__ __forceinline__ void singular_pair(const DevMesh& m, double k, int ns
       Q[a][c] = m.verts[3 * tp.q[a] + c];
     }
   // P0 == Q0 for every touching kind, so x - y = (x - P0) - (y - Q0) exactly.
+  double EP[2][3], EQ[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    EP[0][c] = P[1][c] - P[0][c];
+    EP[1][c] = P[2][c] - P[1][c];
+    EQ[0][c] = Q[1][c] - Q[0][c];
+    EQ[1][c] = Q[2][c] - Q[1][c];
+  }
   const int n2 = nss * nss, n4 = n2 * n2;
   double acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.0;
-  for (int idx = threadIdx.x; idx < n4; idx += blockDim.x) {
+  for (int idx = lane; idx < n4; idx += 32) {
     int a = idx / (n2 * nss), b = (idx / n2) % nss, c = (idx / nss) % nss, d = idx % nss;
     double xi = c_glx[a], e1 = c_glx[b], e2 = c_glx[c], e3 = c_glx[d];
     double w4 = c_glw[a] * c_glw[b] * c_glw[c] * c_glw[d];
@@ -267,8 +324,8 @@ __device__ __forceinline__ void singular_pair(const DevMesh& m, double k, int ns
           {xi, xi * e1 * (1 - e2), xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3)}};
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        chi_rel(P, s[j][0], s[j][1], x);
-        chi_rel(Q, s[j][2], s[j][3], y);
+        chi_rel(EP, s[j][0], s[j][1], x);
+        chi_rel(EQ, s[j][2], s[j][3], y);
         ss_accumulate(k, x, y, w, acc);
       }
     } else if (tp.kind == 2) {
@@ -281,59 +338,66 @@ __device__ __forceinline__ void singular_pair(const DevMesh& m, double k, int ns
           {xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3), xi, xi * e1 * e2, w1}};
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        chi_rel(P, s[j][0], s[j][1], x);
-        chi_rel(Q, s[j][2], s[j][3], y);
+        chi_rel(EP, s[j][0], s[j][1], x);
+        chi_rel(EQ, s[j][2], s[j][3], y);
         ss_accumulate(k, x, y, s[j][4], acc);
       }
     } else {
       double w = w4 * xi * xi * xi * e2;
-      chi_rel(P, xi, xi * e1, x);
-      chi_rel(Q, xi * e2, xi * e2 * e3, y);
+      chi_rel(EP, xi, xi * e1, x);
+      chi_rel(EQ, xi * e2, xi * e2 * e3, y);
       ss_accumulate(k, x, y, w, acc);
-      chi_rel(P, xi * e2, xi * e2 * e3, x);
-      chi_rel(Q, xi, xi * e1, y);
+      chi_rel(EP, xi * e2, xi * e2 * e3, x);
+      chi_rel(EQ, xi, xi * e1, y);
       ss_accumulate(k, x, y, w, acc);
     }
   }
-  // block reduction of the 16 moments
-  __shared__ double red[4][16];
+  // butterfly reduction: every lane ends with the 16 sums
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
-    double v = acc[i];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    acc[i] = v;
+    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
   }
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int i = 0; i < 16; ++i) red[threadIdx.x >> 5][i] = acc[i];
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (lane >= 9) return;
+  // lane = 3 i + j: entry (i, j) of the block,
+  //   A_ij = c_i c'_j [XY - q_j.X - p_i.Y + (p_i.q_j) I0],  Phi_ij = d_i d'_j I0,
+  //   Z_ij += -ik A_ij + (i/k) Phi_ij,
+  // with p_i, q_j the opposite vertices relative to P0 = Q0
+  const int i = lane / 3, j = lane % 3;
   const int t1 = tp.t1, t2 = tp.t2;
   const double jac = 4.0 * m.tri_area[t1] * m.tri_area[t2] * kInv4Pi;
-  double mom[16];
-  for (int i = 0; i < 16; ++i) mom[i] = (red[0][i] + red[1][i] + red[2][i] + red[3][i]) * jac;
-  double p[3][3], q[3][3], c1[3], d1[3], c2[3], d2[3];
-  int e1[3], e2[3];
-  for (int i = 0; i < 3; ++i) {
-    int a = m.tris[3 * t1 + i], b = m.tris[3 * t2 + i];
-    for (int c = 0; c < 3; ++c) {
-      p[i][c] = m.verts[3 * a + c] - P[0][c];
-      q[i][c] = m.verts[3 * b + c] - Q[0][c];
-    }
-    c1[i] = m.tri_coef[3 * t1 + i];
-    d1[i] = m.tri_div[3 * t1 + i];
-    c2[i] = m.tri_coef[3 * t2 + i];
-    d2[i] = m.tri_div[3 * t2 + i];
-    e1[i] = m.tri_edge[3 * t1 + i];
-    e2[i] = m.tri_edge[3 * t2 + i];
+  const int a = m.tris[3 * t1 + i], b = m.tris[3 * t2 + j];
+  double pi_[3], qj[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    pi_[c] = m.verts[3 * a + c] - P[0][c];
+    qj[c] = m.verts[3 * b + c] - Q[0][c];
   }
-  scatter_block(k, mom, p, q, c1, d1, c2, d2, e1, e2, Z, ldz, t1 != t2);
+  double mo[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) mo[q] = acc[q] * jac;
+  const double qXr = qj[0] * mo[2] + qj[1] * mo[4] + qj[2] * mo[6];
+  const double qXi = qj[0] * mo[3] + qj[1] * mo[5] + qj[2] * mo[7];
+  const double pYr = pi_[0] * mo[8] + pi_[1] * mo[10] + pi_[2] * mo[12];
+  const double pYi = pi_[0] * mo[9] + pi_[1] * mo[11] + pi_[2] * mo[13];
+  const double pq = pi_[0] * qj[0] + pi_[1] * qj[1] + pi_[2] * qj[2];
+  const double ar = mo[14] - qXr - pYr + pq * mo[0];
+  const double ai = mo[15] - qXi - pYi + pq * mo[1];
+  const double cc = m.tri_coef[3 * t1 + i] * m.tri_coef[3 * t2 + j];
+  const double dk = m.tri_div[3 * t1 + i] * m.tri_div[3 * t2 + j] * kinv;
+  // -ik (ar + i ai) = k ai - i k ar;  (i/k) dd (I0r + i I0i) = -(dd/k) I0i + i (dd/k) I0r
+  const double zr = k * cc * ai - dk * mo[1];
+  const double zi = -k * cc * ar + dk * mo[0];
+  const int e1 = m.tri_edge[3 * t1 + i], e2 = m.tri_edge[3 * t2 + j];
+  atomic_add_c(Z + 2 * (int64_t(e1) * ldz + e2), zr, zi);
+  if (t1 != t2) atomic_add_c(Z + 2 * (int64_t(e2) * ldz + e1), zr, zi);
 }
 
+// four touching pairs per 128-thread CTA, one per warp
 template <typename OutT>
 __global__ void __launch_bounds__(128) efie_singular_kernel(DevMesh m, double k, int nss, OutT* Z, int64_t ldz) {
-  singular_pair(m, k, nss, Z, ldz, blockIdx.x);
+  const int64_t pair = int64_t(blockIdx.x) * 4 + (threadIdx.x >> 5);
+  if (pair < m.ntouch) singular_pair(m, k, nss, Z, ldz, pair);
 }
 
 // Batched forms over many meshes: a flat grid whose block (singular) or thread (RHS) index
@@ -362,10 +426,11 @@ __device__ __forceinline__ int batch_find(const BatchItem* items, int n, int64_t
 }
 
 __global__ void __launch_bounds__(128) efie_singular_batched_kernel(const BatchItem* __restrict__ items, int nitems,
-                                                                    int nss) {
-  const int i = batch_find(items, nitems, blockIdx.x, false);
-  const BatchItem& it = items[i];
-  singular_pair(it.m, it.k, nss, it.Z, it.ldz, int64_t(blockIdx.x) - it.pair_start);
+                                                                    int64_t pairs, int nss) {
+  const int64_t w = int64_t(blockIdx.x) * 4 + (threadIdx.x >> 5);  // one pair per warp
+  if (w >= pairs) return;
+  const BatchItem& it = items[batch_find(items, nitems, w, false)];
+  singular_pair(it.m, it.k, nss, it.Z, it.ldz, w - it.pair_start);
 }
 
 // ------------------------------------------------------------------ right-hand side
@@ -559,9 +624,9 @@ cudaError_t launch_assemble_singular(const DevMesh& m, double k, int nss, bool f
   if (m.ntouch == 0) return cudaSuccess;
   ProfScope prof("asm_singular", s, double(m.ntouch));
   if (fp32_out)
-    efie_singular_kernel<float><<<unsigned(m.ntouch), 128, 0, s>>>(m, k, nss, static_cast<float*>(Z), ldz);
+    efie_singular_kernel<float><<<blocks_for(m.ntouch, 4), 128, 0, s>>>(m, k, nss, static_cast<float*>(Z), ldz);
   else
-    efie_singular_kernel<double><<<unsigned(m.ntouch), 128, 0, s>>>(m, k, nss, static_cast<double*>(Z), ldz);
+    efie_singular_kernel<double><<<blocks_for(m.ntouch, 4), 128, 0, s>>>(m, k, nss, static_cast<double*>(Z), ldz);
   return launched();
 }
 
@@ -651,7 +716,7 @@ cudaError_t launch_singular_rhs_batched(const DevMesh* const* meshes, const doub
   const BatchItem* di = static_cast<const BatchItem*>(d_items);
   if (pairs > 0) {
     ProfScope prof("asm_singular", s, double(pairs));
-    efie_singular_batched_kernel<<<unsigned(pairs), 128, 0, s>>>(di, nmesh, nss);
+    efie_singular_batched_kernel<<<blocks_for(pairs, 4), 128, 0, s>>>(di, nmesh, pairs, nss);
     e = launched();
     if (e != cudaSuccess) return e;
   }
