@@ -384,6 +384,19 @@ fosb_status fosb_mesh_perturb(fosb_mesh base, const double* xi, double t, fosb_m
 fosb_status fosb_mc_moments(int64_t n3, int64_t nsamp, const void* Fs, int64_t ldf, const void* F0, double t,
                             void* mean, void* cov, int64_t ldc, void* pcov, int64_t ldp, void* stream);
 
+/* ---- FP64-class complex matrix product ------------------------------------------------
+ * C = A B for complex128 row-major A (M x K, lda), B (K x N, ldb), C (M x N, ldc) (device),
+ * accurate to a few units of 2^-52 of (|A||B|)_ij, computed without the FP64 pipe (1.25 TFLOP/s
+ * on this part) by either of the two products behind the refinement residuals:
+ *   method 0: exact digit splitting on the bf16 tensor cores: each row of A and column of B is
+ *             scaled by a power of two and cut into seven balanced base-256 digits; the digit
+ *             products up to order 6 are summed exactly (integer order sums per 64-wide k chunk);
+ *   method 1: float-float (pairs of floats) on the FP32 pipe.
+ * Allocates its digit scratch stream-ordered; synchronises `stream`.
+ * Errors: FOSB_ERR_INVALID_ARG, FOSB_ERR_TIMEOUT. */
+fosb_status fosb_zgemm_fp64class(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                                 int64_t ldb, void* C, int64_t ldc, int method, void* stream);
+
 /* ---- Diagnostics: bounded device waits ---------------------------------------------
  * Every spin-wait of the library's kernels gives up after a number of polls, sets the
  * status word of the call to FOSB_ERR_TIMEOUT and returns, so the call reports

@@ -74,7 +74,8 @@ def lib():
                      "fosb_covariance", "fosb_farfield_moments", "fosb_rcs_monostatic",
                      "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read", "fosb_rcs_moments",
                      "fosb_debug_set_wait_limit", "fosb_peak_microbench", "fosb_assemble_efie_batched",
-                     "fosb_solve_batched", "fosb_field_samples", "fosb_mesh_perturb", "fosb_mc_moments"):
+                     "fosb_solve_batched", "fosb_field_samples", "fosb_mesh_perturb", "fosb_mc_moments",
+                     "fosb_zgemm_fp64class"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -363,3 +364,12 @@ def mc_moments(Fs, F0, t: float, mean=None, cov=None, pcov=None, stream=None):
                                  ctypes.c_int64(0 if cov is None else _ld(cov)), None if pcov is None else _ptr(pcov),
                                  ctypes.c_int64(0 if pcov is None else _ld(pcov)), _stream(stream)))
     return mean, cov, pcov
+
+
+def zgemm_fp64class(A, B, C, method: int = 0, stream=None):
+    """fosb_zgemm_fp64class: C = A B (complex128) with FP64-class accuracy, by exact digit
+    splitting on the bf16 tensor cores (method 0) or float-float on the FP32 pipe (1)."""
+    _check(lib().fosb_zgemm_fp64class(ctypes.c_int64(A.shape[0]), ctypes.c_int64(B.shape[1]), ctypes.c_int64(A.shape[1]),
+                                      _ptr(A), ctypes.c_int64(_ld(A)), _ptr(B), ctypes.c_int64(_ld(B)), _ptr(C),
+                                      ctypes.c_int64(_ld(C)), ctypes.c_int(method), _stream(stream)))
+    return C

@@ -545,3 +545,34 @@ cudaError_t oz_gemm(int64_t M, int64_t N, int64_t K, double alpha_re, double alp
 }
 
 }  // namespace fosb
+
+extern "C" fosb_status fosb_zgemm_fp64class(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                                            int64_t ldb, void* C, int64_t ldc, int method, void* stream) {
+  using namespace fosb;
+  if (M < 0 || N < 0 || K < 0 || (M > 0 && N > 0 && (!A || !B || !C)) || lda < K || ldb < N || ldc < N)
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_zgemm_fp64class: bad arguments");
+  if (method != 0 && method != 1) return fail(FOSB_ERR_INVALID_ARG, "fosb_zgemm_fp64class: method must be 0 or 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (M == 0 || N == 0) return FOSB_OK;
+  if (K == 0) {
+    FOSB_CUDA(cudaMemset2DAsync(C, ldc * 16, 0, N * 16, M, s));
+    return FOSB_OK;
+  }
+  if (method == 1) {
+    FOSB_CUDA(gemm_c128_ff(OP_N, OP_N, M, N, K, 1.0, 0.0, A, lda, B, ldb, 0.0, C, ldc, s));
+    return FOSB_OK;
+  }
+  Scratch dig(s), ex(s), st(s);
+  FOSB_CUDA(dig.alloc(oz_a_bytes(M, K)));
+  FOSB_CUDA(ex.alloc(sizeof(int) * size_t(M)));
+  FOSB_CUDA(st.alloc(sizeof(int)));
+  FOSB_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+  FOSB_CUDA(oz_prepare_a(A, M, K, lda, dig.p, ex.as<int>(), s));
+  FOSB_CUDA(oz_gemm(M, N, K, 1.0, 0.0, dig.p, ex.as<int>(), B, ldb, 0.0, C, ldc, st.as<int>(), s));
+  int status = 0;
+  FOSB_CUDA(cudaMemcpyAsync(&status, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  if (status == FOSB_ERR_TIMEOUT) return fail(FOSB_ERR_TIMEOUT, "fosb_zgemm_fp64class: tensor-core wait timed out");
+  return FOSB_OK;
+}
+

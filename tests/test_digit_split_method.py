@@ -8,7 +8,8 @@ on the CPU with exact integer and rational arithmetic (no GPU, no oracle):
     (g + 1) digit pairs, two real products each, stay below 2^24 (exact in FP32);
   * keeping the orders g = s + t <= 6 bounds the product error at a few units of 2^-52 of
     sum |Z||X| on rows and columns of very different scale, and dropping order 6 does not.
-The GPU kernels implement exactly these steps; their own parity runs through the solves.
+The GPU kernels implement these steps; tests/test_gpu_digit_gemm.py checks them directly against
+the exact rational product on these operands, and the refined solves use them throughout.
 """
 import math
 import random
