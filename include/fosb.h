@@ -386,12 +386,14 @@ fosb_status fosb_mc_moments(int64_t n3, int64_t nsamp, const void* Fs, int64_t l
 
 /* ---- FP64-class complex matrix product ------------------------------------------------
  * C = A B for complex128 row-major A (M x K, lda), B (K x N, ldb), C (M x N, ldc) (device),
- * accurate to a few units of 2^-52 of (|A||B|)_ij, computed without the FP64 pipe (1.25 TFLOP/s
- * on this part) by either of the two products behind the refinement residuals:
+ * computed without the FP64 pipe (1.25 TFLOP/s on this part) by either of the two products
+ * behind the refinement residuals:
  *   method 0: exact digit splitting on the bf16 tensor cores: each row of A and column of B is
  *             scaled by a power of two and cut into seven balanced base-256 digits; the digit
- *             products up to order 6 are summed exactly (integer order sums per 64-wide k chunk);
- *   method 1: float-float (pairs of floats) on the FP32 pipe.
+ *             products up to order 6 are summed exactly (integer order sums per 64-wide k chunk):
+ *             within a few units of 2^-52 of (|A||B|)_ij, independent of K;
+ *   method 1: float-float (pairs of floats, about 48 significant bits) on the FP32 pipe:
+ *             within K 2^-48 of (|A||B|)_ij.
  * Allocates its digit scratch stream-ordered; synchronises `stream`.
  * Errors: FOSB_ERR_INVALID_ARG, FOSB_ERR_TIMEOUT. */
 fosb_status fosb_zgemm_fp64class(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
