@@ -55,9 +55,10 @@ WORKLOADS = {
 }
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
+LU_BLOCK = 256  # column block of the complex64 LU: every trailing update has K = 256
 # DRAM bytes (read + write) per complex64 output element of one tcgen05 LU-update launch,
 # from the ncu capture summarised in profiles/ (C is read and written once: 16 B algorithmic)
-LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (545.124352e6 + 381.822208e6) / 7552.0**2  # 16.25 B
+LU_UPDATE_DRAM_BYTES_PER_OUTPUT = None
 
 
 def _peaks():
@@ -202,8 +203,8 @@ def run_fosb(args):
     # after it, a profiled pass of two steps: per-phase and per-kernel-family CUDA events
     import ctypes
 
-    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "trsm_update",
-                "oz_prep", "getrs"]
+    families = ["lu_update", "lu_update64", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz",
+                "trsm_update", "oz_prep", "getrs"]
     for fam in families:  # clear earlier records
         F.lib().fosb_profile_read(fam.encode(), None, None, None)
     timers = {}
@@ -245,6 +246,9 @@ def run_fosb(args):
                       "split once per block and bulk-copied; the split kernels are timed with it)",
                       f"TF32 dense = bf16 sustained {bf16} ({bf16_src}) x 1.1/2.25; work = useful complex flops "
                       "8MNK (3xTF32 executes 3x that on the tensor pipe, so frac <= 1/3)"),
+        "lu_update64": ("tensor", 1.0, tf32_peak,
+                        "cgemm_update_tc_ws_kernel (the K = 64 updates inside each 256-column block of the LU)",
+                        "work = useful complex flops 8MNK"),
         "asm_regular": ("alu", 27.0, fp_peak,
                         "efie_regular_ff_kernel" if arith == F.ASM_FF else "efie_regular_kernel<double>",
                         "27 algorithmic FP ops per point pair; peak = the FP32 (float-float) or FP64 FMA pipe "
@@ -279,8 +283,8 @@ def run_fosb(args):
     if dom == "lu_update" and st["launches_per_step"] > 0:
         # DRAM bytes per launch from the ncu capture (bytes per output element of C, see
         # profiles/), scaled to the average launch of the timed region: C elements = flops /
-        # (8 K) with K = 128, the depth of the trailing updates that carry most of the flops
-        avg_outputs = st["work_per_step"] / (8.0 * 128.0 * st["launches_per_step"])
+        # (8 K) with K = 256, the depth of every trailing update of the 256-column blocking
+        avg_outputs = st["work_per_step"] / (8.0 * LU_BLOCK * st["launches_per_step"])
         if LU_UPDATE_DRAM_BYTES_PER_OUTPUT is not None:
             roofline["traffic"] = round(LU_UPDATE_DRAM_BYTES_PER_OUTPUT * avg_outputs)
         roofline["algorithmic_bytes"] = round(16.0 * avg_outputs)
@@ -394,7 +398,8 @@ def run_batched(args):
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, ws, "cuda")
     # kernel-family events from a separate 2-step pass after the timed region
-    families = ["lu_update", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "oz_prep", "getrs"]
+    families = ["lu_update", "lu_update64", "lu_panel", "asm_regular", "asm_singular", "gemm_ff", "gemm_oz", "oz_prep",
+                "getrs"]
     for f in families:
         F.lib().fosb_profile_read(f.encode(), None, None, None)
     F.lib().fosb_profile_enable(1)
@@ -410,6 +415,7 @@ def run_batched(args):
     peaks = _peaks()
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     model = {"lu_update": ("tensor", 1.0, bf16 * TF32_PER_BF16, "cgemm_update_split_kernel"),
+             "lu_update64": ("tensor", 1.0, bf16 * TF32_PER_BF16, "cgemm_update_tc_ws_kernel"),
              "asm_regular": ("alu", 27.0, upeaks["fp32"], "efie_regular_ff_batched_kernel (persistent, ticketed tiles)"),
              "lu_panel": ("latency", 1.0, None, "tslu_gepp_kernel"),
              "asm_singular": ("alu", 1.0, None, "efie_singular_batched_kernel"),

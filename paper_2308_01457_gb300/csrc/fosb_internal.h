@@ -184,10 +184,14 @@ cudaError_t gemm(int opA, int opB, int64_t M, int64_t N, int64_t K, double alpha
                  int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s);
 // C (M x N) -= A (M x K) B (K x N), complex64 row-major, tcgen05 tensor cores with 3xTF32;
 // a bounded mbarrier wait that gives up sets *status = FOSB_ERR_TIMEOUT.  family names the
-// timing record (fosb_profile_read): factor updates and solve sweeps are timed apart
+// timing record (fosb_profile_read): the LU's K = 64 updates ("lu_update64") and the solve
+// sweeps ("trsm_update") are timed apart from the K = kLuBlock trailing updates ("lu_update")
 cudaError_t cgemm_update_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
-                            void* C, int64_t ldc, int* status, cudaStream_t s, const char* family = "lu_update");
-// The same update for K <= 128 with A and B split once into bulk-copy images
+                            void* C, int64_t ldc, int* status, cudaStream_t s, const char* family);
+// Column block of the complex64 LU (four 64-column panels per block, one trailing update
+// with K = kLuBlock per block).
+constexpr int kLuBlock = 256;
+// The same update for K <= kLuBlock with A and B split once into bulk-copy images
 // (tc_update.cu): workspaces of update_split_a_bytes(M) and update_split_b_bytes(N) bytes.
 size_t update_split_a_bytes(int64_t M);
 size_t update_split_b_bytes(int64_t N);

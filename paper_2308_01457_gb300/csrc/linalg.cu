@@ -1304,34 +1304,41 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
     return launched();
   };
   if constexpr (sizeof(T) == 4) {
-    // complex64 factors: outer blocks of 128 columns, each factored as two 64-column
-    // panels, so that the tensor-core trailing update runs with K = 128 and streams the
-    // trailing matrix half as often as 64-column blocking would.
-    const int64_t NB = 128;
+    // complex64 factors: outer blocks of NB = 256 columns, each factored as four 64-column
+    // panels (each panel's L updates the block's columns to its right), then the block's U12
+    // rows panel by panel, then one tensor-core trailing update with K = 256, so the trailing
+    // matrix streams through HBM a quarter as often as 64-column blocking would.
+    const int64_t NB = kLuBlock;
     for (int64_t j0 = 0; j0 < n && st == FOSB_OK; j0 += NB) {
       const int jb = int(std::min<int64_t>(NB, n - j0));
-      const int jb1 = std::min(jb, nb), jb2 = jb - jb1;
-      V* Ap = A + j0 * lda + j0;
-      cudaError_t e = panel_step(j0, jb1);
-      if (e == cudaSuccess && jb2 > 0) {
-        // right half of the block: U rows of the first panel, then its rank-64 update
-        e = trsm_lower(Ap, jb1, Ap + jb1, jb2);
-        if (e == cudaSuccess)
-          e = cgemm_update_tc(n - j0 - jb1, jb2, jb1, Ap + jb1 * lda, lda, Ap + jb1, lda, Ap + jb1 * lda + jb1, lda,
-                              d_status, s);
-        if (e == cudaSuccess) e = panel_step(j0 + jb1, jb2);
+      V* Ab = A + j0 * lda + j0;
+      cudaError_t e = cudaSuccess;
+      for (int p0 = 0; p0 < jb && e == cudaSuccess; p0 += nb) {
+        const int pw = std::min(nb, jb - p0), right = jb - p0 - pw;
+        e = panel_step(j0 + p0, pw);
+        if (e == cudaSuccess && right > 0) {
+          V* Dp = Ab + int64_t(p0) * lda + p0;  // the panel's diagonal block
+          e = trsm_lower(Dp, pw, Dp + pw, right);
+          if (e == cudaSuccess)
+            e = cgemm_update_tc(n - j0 - p0 - pw, right, pw, Dp + int64_t(pw) * lda, lda, Dp + pw, lda,
+                                Dp + int64_t(pw) * lda + pw, lda, d_status, s, "lu_update64");
+        }
       }
       const int64_t rest = n - j0 - jb;
       if (e == cudaSuccess && rest > 0) {
-        // U12 = L11^{-1} A12 for the 128-row block (two 64-row sweeps and the coupling update)
-        e = trsm_lower(Ap, jb1, Ap + jb, rest);
-        if (e == cudaSuccess && jb2 > 0)
-          e = cgemm_update_tc(jb2, rest, jb1, Ap + jb1 * lda, lda, Ap + jb, lda, Ap + jb1 * lda + jb, lda, d_status,
-                              s);
-        if (e == cudaSuccess && jb2 > 0) e = trsm_lower(Ap + jb1 * lda + jb1, jb2, Ap + jb1 * lda + jb, rest);
+        // U12 = L11^{-1} A12 for the block's rows, one 64-row sweep and its coupling update per panel
+        for (int p0 = 0; p0 < jb && e == cudaSuccess; p0 += nb) {
+          const int pw = std::min(nb, jb - p0), below = jb - p0 - pw;
+          V* Dp = Ab + int64_t(p0) * lda + p0;
+          V* Up = Ab + int64_t(p0) * lda + jb;
+          e = trsm_lower(Dp, pw, Up, rest);
+          if (e == cudaSuccess && below > 0)
+            e = cgemm_update_tc(below, rest, pw, Dp + int64_t(pw) * lda, lda, Up, lda, Up + int64_t(pw) * lda, lda,
+                                d_status, s, "lu_update64");
+        }
         if (e == cudaSuccess)
-          e = cgemm_update_tc_split(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda,
-                                    d_status, ws_a, ws_b, s);
+          e = cgemm_update_tc_split(rest, rest, jb, Ab + int64_t(jb) * lda, lda, Ab + jb, lda,
+                                    Ab + int64_t(jb) * lda + jb, lda, d_status, ws_a, ws_b, s);
       }
       if (e != cudaSuccess) st = cuda_fail(e, "getrf: blocked step");
     }
@@ -1406,7 +1413,8 @@ fosb_status getrf_external_scratch(void* Av, int64_t n, int64_t lda, int32_t* ip
       trsv_warp_kernel<T><<<cdiv(rest, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(Ap, lda, jb, 0, Ap + jb, lda, rest);
       note_launches(1);
       if constexpr (sizeof(T) == 4)
-        FOSB_CUDA(cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s));
+        FOSB_CUDA(cgemm_update_tc(rest, rest, jb, Ap + jb * lda, lda, Ap + jb, lda, Ap + jb * lda + jb, lda, d_status, s,
+                                  "lu_update64"));
       else
         FOSB_CUDA(gemm<T>(OP_N, OP_N, rest, rest, jb, -1.0, 0.0, Ap + jb * lda, lda, Ap + jb, lda, 1.0,
                         Ap + jb * lda + jb, lda, s));

@@ -3,7 +3,7 @@
 //   x y ~ x_b y_b + x_b y_s + x_s y_b).
 //
 // Split once, copied many times.  A (L21, M x K) and B (U12, K x N) are each split by one
-// pass per 128-column block into the exact shared-memory image the MMAs read: for every
+// pass per column block (K <= 256) into the exact shared-memory image the MMAs read: for every
 // 128-row (or 128-column) tile and 8-wide k-slab, 4 KB "parts" in the canonical no-swizzle
 // K-major layout (8-row x 16-byte core matrices; 128 B between the two core matrices of a
 // slab, 256 B between 8-row groups).  Per slab, A has 4 parts (Re_b, Re_s, Im_b, Im_s) and
@@ -38,7 +38,7 @@ namespace fosb {
 namespace {
 
 constexpr int U_TM = 128, U_TN = 128;          // tile: 128 rows x 128 complex columns
-constexpr int U_KB = 128;                      // k extent of a split block (slabs per tile: 16)
+constexpr int U_KB = kLuBlock;                 // largest k extent of a split block (32 slabs)
 constexpr int U_SLABS = U_KB / 8;
 constexpr int U_PART = 4096;                   // one 128 x 8 tf32 part
 constexpr int U_ABYTES = 4 * U_PART;           // A parts of one slab
@@ -131,34 +131,36 @@ __device__ __forceinline__ void u_cp_commit() { asm volatile("cp.async.commit_gr
 __device__ __forceinline__ void u_cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------- splits
-// A (M x K, lda), K <= 128: out[(rt * 16 + s) * 16 KB + p * 4 KB + part_off(r, k8)], parts
-// Re_b, Re_s, Im_b, Im_s; zero outside M x K.  One thread per (row, k) of the padded tile grid.
-__global__ void split_a_kernel(int64_t M, int K, const float2* __restrict__ A, int64_t lda, float* __restrict__ out,
-                               int64_t rows_pad) {
+// A (M x K, lda), K <= 256 in nslab = ceil(K / 8) slabs: out[(rt * nslab + s) * 16 KB + p * 4 KB +
+// part_off(r, k8)], parts Re_b, Re_s, Im_b, Im_s; zero outside M x K.  One thread per (row, k)
+// of the padded tile grid.
+__global__ void split_a_kernel(int64_t M, int K, int nslab, const float2* __restrict__ A, int64_t lda,
+                               float* __restrict__ out, int64_t rows_pad) {
+  const int kp = nslab * 8;
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= rows_pad * U_KB) return;
-  const int64_t row = e / U_KB;
-  const int k = int(e % U_KB);
+  if (e >= rows_pad * kp) return;
+  const int64_t row = e / kp;
+  const int k = int(e % kp);
   const float2 v = (row < M && k < K) ? A[row * lda + k] : make_float2(0.f, 0.f);
   const float rb = tf32r(v.x), ib = tf32r(v.y);
-  float* base = out + ((row / U_TM) * U_SLABS + k / 8) * (U_ABYTES / 4) + part_off(int(row % U_TM), k & 7) / 4;
+  float* base = out + ((row / U_TM) * nslab + k / 8) * (U_ABYTES / 4) + part_off(int(row % U_TM), k & 7) / 4;
   base[0 * U_PART / 4] = rb;
   base[1 * U_PART / 4] = tf32r(v.x - rb);
   base[2 * U_PART / 4] = ib;
   base[3 * U_PART / 4] = tf32r(v.y - ib);
 }
-// B (K x N, ldb), K <= 128: out[(ct * 16 + s) * 24 KB + p * 4 KB + part_off(c, k8)], parts
+// B (K x N, ldb), K <= 256: out[(ct * nslab + s) * 24 KB + p * 4 KB + part_off(c, k8)], parts
 // Br_b, Bi_b, -Br_b, Br_s, Bi_s, -Br_s; zero outside K x N.  Threads run along N (coalesced).
-__global__ void split_b_kernel(int64_t N, int K, const float2* __restrict__ B, int64_t ldb, float* __restrict__ out,
-                               int64_t cols_pad) {
+__global__ void split_b_kernel(int64_t N, int K, int nslab, const float2* __restrict__ B, int64_t ldb,
+                               float* __restrict__ out, int64_t cols_pad) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= cols_pad * U_KB) return;
+  if (e >= cols_pad * nslab * 8) return;
   const int k = int(e / cols_pad);
   const int64_t col = e % cols_pad;
   const float2 v = (col < N && k < K) ? B[int64_t(k) * ldb + col] : make_float2(0.f, 0.f);
   const float rb = tf32r(v.x), ib = tf32r(v.y);
   const float rs = tf32r(v.x - rb), is = tf32r(v.y - ib);
-  float* base = out + ((col / U_TN) * U_SLABS + k / 8) * (U_BBYTES / 4) + part_off(int(col % U_TN), k & 7) / 4;
+  float* base = out + ((col / U_TN) * nslab + k / 8) * (U_BBYTES / 4) + part_off(int(col % U_TN), k & 7) / 4;
   base[0 * U_PART / 4] = rb;
   base[1 * U_PART / 4] = ib;
   base[2 * U_PART / 4] = -rb;
@@ -234,8 +236,8 @@ __global__ void __launch_bounds__(U_THREADS, 1)
           unsigned char* sa = smem + st * U_STAGE;
           const uint32_t fb = su32(&bar_full[st]);
           u_expect_tx(fb, U_STAGE);
-          u_bulk(su32(sa), As + (rt * U_SLABS + s) * int64_t(U_ABYTES), U_ABYTES, fb);
-          u_bulk(su32(sa + U_ABYTES), Bs + (ct * U_SLABS + s) * int64_t(U_BBYTES), U_BBYTES, fb);
+          u_bulk(su32(sa), As + (rt * nslab + s) * int64_t(U_ABYTES), U_ABYTES, fb);
+          u_bulk(su32(sa + U_ABYTES), Bs + (ct * nslab + s) * int64_t(U_BBYTES), U_BBYTES, fb);
         }
       }
       // wait for every copy issued here that the MMA thread may not have consumed
@@ -400,7 +402,7 @@ inline unsigned ucdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); 
 size_t update_split_a_bytes(int64_t M) { return size_t((M + U_TM - 1) / U_TM) * U_SLABS * U_ABYTES; }
 size_t update_split_b_bytes(int64_t N) { return size_t((N + U_TN - 1) / U_TN) * U_SLABS * U_BBYTES; }
 
-// C (M x N) -= A (M x K) B (K x N), complex64 row-major, K <= 128: split A and B once into
+// C (M x N) -= A (M x K) B (K x N), complex64 row-major, K <= kLuBlock: split A and B once into
 // the workspaces (update_split_a_bytes(M), update_split_b_bytes(N) bytes, 16-byte aligned),
 // then the bulk-copy-fed tcgen05 update.
 cudaError_t cgemm_update_tc_split(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
@@ -423,12 +425,12 @@ cudaError_t cgemm_update_tc_split(int64_t M, int64_t N, int64_t K, const void* A
   const int64_t RT = (M + U_TM - 1) / U_TM, CT = (N + U_TN - 1) / U_TN;
   const int64_t rows_pad = RT * U_TM, cols_pad = CT * U_TN;
   ProfScope prof("lu_update", s, 8.0 * double(M) * double(N) * double(K));  // the splits are part of it
-  split_a_kernel<<<ucdiv(rows_pad * U_KB, 256), 256, 0, s>>>(M, int(K), static_cast<const float2*>(A), lda,
-                                                            static_cast<float*>(ws_a), rows_pad);
-  split_b_kernel<<<ucdiv(cols_pad * U_KB, 256), 256, 0, s>>>(N, int(K), static_cast<const float2*>(B), ldb,
-                                                            static_cast<float*>(ws_b), cols_pad);
+  const int nslab = int((K + 7) / 8);  // tiles packed with exactly nslab slabs each
+  split_a_kernel<<<ucdiv(rows_pad * nslab * 8, 256), 256, 0, s>>>(M, int(K), nslab, static_cast<const float2*>(A), lda,
+                                                                static_cast<float*>(ws_a), rows_pad);
+  split_b_kernel<<<ucdiv(cols_pad * nslab * 8, 256), 256, 0, s>>>(N, int(K), nslab, static_cast<const float2*>(B), ldb,
+                                                                static_cast<float*>(ws_b), cols_pad);
   note_launches(2);
-  const int nslab = int((K + 7) / 8);
   const unsigned grid = unsigned(std::min<int64_t>(RT * CT, std::max(nsm[dev], 1)));
   const int vec_ok = (reinterpret_cast<uintptr_t>(C) % 16 == 0) && (ldc % 2 == 0);
   cgemm_update_split_kernel<<<grid, U_THREADS, U_SMEM, s>>>(M, N, nslab, static_cast<const unsigned char*>(ws_a),

@@ -185,6 +185,32 @@ def test_solve_multiple_rhs_and_ragged_sizes():
     assert _rel(B2.cpu().numpy(), Xo) < 1e-8
 
 
+@pytest.mark.parametrize("n", [600, 700, 1030])
+def test_complex64_lu_spans_column_blocks_and_ragged_panels(n):
+    """The complex64 LU works in 256-column blocks of four 64-column panels with one
+    K = 256 trailing update per block: n = 600, 700, 1030 leave a last block of 88, 188
+    and 6 columns (ragged panels) and ragged 128-row tiles.  A row-permuted, diagonally
+    dominant matrix forces a pivot on every column; a plain complex Gaussian matrix
+    pivots freely.  MIXED solves agree with LAPACK at 1e-10; FP32 (complex64 factors,
+    no refinement) at 1e-4."""
+    rng = np.random.default_rng(n)
+    G = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(2 * n)
+    Ap = (G + 2.0 * np.eye(n))[rng.permutation(n)]
+    Bh = rng.standard_normal((n, 5)) + 1j * rng.standard_normal((n, 5))
+    for Ah in (Ap, G * math.sqrt(n)):
+        Xo = np.linalg.solve(Ah, Bh)
+        A = torch.tensor(Ah, dtype=C128, device=DEV)
+        B = torch.tensor(Bh, dtype=C128, device=DEV)
+        X = torch.zeros_like(B)
+        F.solve(F.factor(A, prec=F.MIXED), B, X)
+        assert _rel(X.cpu().numpy(), Xo) < 1e-10
+        if Ah is Ap:
+            A32, B32 = A.to(C64), B.to(C64)
+            X32 = torch.zeros_like(B32)
+            F.solve(F.factor(A32, prec=F.FP32), B32, X32)
+            assert _rel(X32.cpu().numpy().astype(np.complex128), Xo) < 1e-4
+
+
 def test_solve_many_rhs_ragged_digit_residual():
     """More than 8 right-hand sides at N >= 256 put the refinement residuals on the
     digit-split tensor-core product. N = 336 (torus 14 x 8) leaves a ragged 80-row tile
