@@ -1293,9 +1293,13 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
       e = launch_panel<T>(A + j0 * lda + j0, n - j0, jb, lda, ipiv + j0, j0, scr, arrivals, cand_data, rowj,
                           d_status, int64_t(G_cap), nsm, s);
     if (e != cudaSuccess) return e;
-    laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
-    note_launches(2);  // panel + row swaps
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+      return tslu_swap(A, n, lda, j0, jb, tslu_scr, s);  // the panel's permutation as row moves
+    } else {
+      laswp_kernel<T><<<cdiv(n, 256), 256, 0, s>>>(A, n, lda, j0, jb, ipiv);
+      note_launches(2);  // panel + row swaps
+      return cudaGetLastError();
+    }
   };
   // X (jb rows x ncols, ld lda) := L^{-1} X with L the unit lower jb x jb block at D
   auto trsm_lower = [&](const V* D, int jb, V* X, int64_t ncols) -> cudaError_t {

@@ -15,12 +15,15 @@
 // The panel stays untouched in global memory until step 3, so every level reads original
 // rows.  Launches are stream-ordered; there is no inter-CTA wait anywhere.
 //
-// Within a CTA the candidate rows sit in shared memory, one per thread, and are factored
-// by blocked partial pivoting in blocks of 8 columns: per step a warp argmax (one reduce
-// and one ballot), one barrier, and the elimination of that column inside the block; per
-// block the trailing columns of its pivot rows by forward substitution with the block's
-// unit lower factor, then one rank-8 update of every remaining row.  This is the same
-// factorisation, with the same pivots, as unblocked partial pivoting.  Rows are never
+// Within a CTA the candidate rows sit in shared memory and are factored by blocked partial
+// pivoting in blocks of 8 columns: per step a warp argmax (one reduction), one
+// barrier among the eight warps that own the rows, an 8-entry argmax across them, and the
+// elimination of that column inside the block (in registers); per block the trailing
+// columns of its pivot rows by forward substitution with the block's unit lower factor,
+// then one rank-8 update of every remaining row by all sixteen warps.  This is the same
+// factorisation as unblocked partial pivoting whose pivot magnitudes are compared on 15
+// mantissa bits (a candidate within a relative 2^-15 of the largest may win the tie as the
+// lower row, so |l| <= 1 + 2^-15).  Rows are never
 // moved: a row that has served as pivot is marked used, keeps its (L, U) entries and is
 // skipped by later updates, so at the end the row chosen at step j holds row j of L \ U.
 #include <cuda_runtime.h>
@@ -34,9 +37,13 @@
 namespace fosb {
 namespace {
 
-constexpr int kTsluRows = 256;  // rows per CTA (one per thread)
+constexpr int kTsluRows = 256;  // rows per CTA
 constexpr int kTsluCols = 64;   // panel width handled (jb <= 64)
 constexpr int kTsluFanIn = kTsluRows / kTsluCols;
+constexpr int kTsluSub = 2;                            // threads per row in the block updates
+constexpr int kTsluThreads = kTsluRows * kTsluSub;     // 512
+constexpr int kTsluStepWarps = kTsluRows / 32;         // warps 0-7 run the pivot steps
+constexpr int kTsluPairs = kTsluCols / 2;              // 16-byte column pairs of a row
 
 __device__ __forceinline__ float2 cinv(float2 v) {
   const float den = v.x * v.x + v.y * v.y;
@@ -48,14 +55,23 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-constexpr int kTsluLd = kTsluCols + 2;  // row pitch in complex values (16-byte aligned rows)
-constexpr int kTsluBlk = 8;              // columns per block of the blocked factorisation
+// Row pitch in complex values: 544 bytes, so the eight threads of a 16-byte access phase in
+// the block updates (four rows x two column pairs) fall in eight distinct bank groups.
+constexpr int kTsluLd = 68;
+constexpr int kTsluBlk = 8;  // columns per block of the blocked factorisation
 constexpr size_t kTsluSmem = size_t(kTsluRows) * kTsluLd * sizeof(float2);
 
 __device__ __forceinline__ void cfms(float2& a, float2 l, float2 u) {  // a -= l u
   a.x -= l.x * u.x - l.y * u.y;
   a.y -= l.x * u.y + l.y * u.x;
 }
+__device__ __forceinline__ void cfms2(float4& a, float2 l, float4 u) {  // both complex values of a pair
+  a.x -= l.x * u.x - l.y * u.y;
+  a.y -= l.x * u.y + l.y * u.x;
+  a.z -= l.x * u.z - l.y * u.w;
+  a.w -= l.x * u.w + l.y * u.z;
+}
+__device__ __forceinline__ void step_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kTsluRows) : "memory"); }
 
 // Leaf mode (in_idx == nullptr): CTA b factors panel rows [b * 256, min(m, (b + 1) * 256)).
 // Tree mode: CTA b factors the nominees of groups [b * 4, min(groups_in, b * 4 + 4)), where
@@ -63,164 +79,225 @@ __device__ __forceinline__ void cfms(float2& a, float2 l, float2 u) {  // a -= l
 // Every CTA writes its pivot rows in order to out_idx[b * 64 ...] and their count to
 // out_cnt[b].  A single-CTA launch is the root: it also writes the factored rows
 // (L11 \ U11, row-major jb x 64) to top and the chosen panel rows to sel.
-__global__ void __launch_bounds__(kTsluRows, 1)
+//
+// The pivot steps of an 8-column block run on warps 0-7 alone, thread t owning row t and
+// keeping the row's eight block columns in registers; a step is one warp argmax, one
+// 256-thread named barrier and an 8-entry argmax across the warps, each a single 32-bit
+// max-reduction.  Each warp's candidate
+// stages its block columns in shared memory before the barrier, so the rows read the pivot
+// row from there and nothing is written back until the block ends.  The block's trailing
+// work (U12 of its pivot rows, the rank-8 update of the other rows) runs on all 512 threads,
+// two per row.
+__global__ void __launch_bounds__(kTsluThreads, 1)
     tslu_gepp_kernel(const float2* __restrict__ A, int64_t lda, int64_t m, int jb, const int* __restrict__ in_idx,
                      const int* __restrict__ in_cnt, int groups_in, int* __restrict__ out_idx, int* __restrict__ out_cnt,
                      float2* __restrict__ top, int* __restrict__ sel) {
   extern __shared__ float4 tslu_raw[];
   float2* sA = reinterpret_cast<float2*>(tslu_raw);  // [kTsluRows][kTsluLd]
   __shared__ int s_rows[kTsluRows];
-  __shared__ unsigned long long s_wk[kTsluRows / 32];
+  __shared__ int s_used[kTsluRows];
+  __shared__ int s_off[kTsluFanIn + 1];
   __shared__ int s_piv[kTsluBlk];
-  __shared__ int s_nr;
+  __shared__ unsigned s_wk[2][kTsluStepWarps];
+  __shared__ float2 s_inv[2][kTsluStepWarps];
+  __shared__ float4 s_stage[2][kTsluStepWarps][kTsluBlk / 2];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool root = gridDim.x == 1;
   // rows of this CTA (panel-row indices)
-  if (t == 0) {
-    int nr = 0;
-    if (in_idx == nullptr) {
-      const int64_t lo = int64_t(blockIdx.x) * kTsluRows;
-      nr = m - lo < kTsluRows ? int(m - lo) : kTsluRows;
-      for (int i = 0; i < nr; ++i) s_rows[i] = int(lo + i);
-    } else {
-      for (int g = blockIdx.x * kTsluFanIn; g < min(groups_in, int(blockIdx.x) * kTsluFanIn + kTsluFanIn); ++g)
-        for (int i = 0; i < in_cnt[g]; ++i) s_rows[nr++] = in_idx[g * kTsluCols + i];
+  int nr;
+  if (in_idx == nullptr) {
+    const int64_t lo = int64_t(blockIdx.x) * kTsluRows;
+    nr = m - lo < kTsluRows ? int(m - lo) : kTsluRows;
+    if (t < nr) s_rows[t] = int(lo + t);
+  } else {
+    const int g0 = blockIdx.x * kTsluFanIn, ng = min(groups_in - g0, kTsluFanIn);
+    if (t == 0) {
+      int acc = 0;
+      for (int g = 0; g < kTsluFanIn; ++g) {
+        s_off[g] = acc;
+        acc += g < ng ? in_cnt[g0 + g] : 0;
+      }
+      s_off[kTsluFanIn] = acc;
     }
-    s_nr = nr;
+    __syncthreads();
+    nr = s_off[kTsluFanIn];
+    if (t < kTsluRows) {
+      const int g = t / kTsluCols, i = t % kTsluCols;
+      if (g < ng && i < s_off[g + 1] - s_off[g]) s_rows[s_off[g] + i] = in_idx[(g0 + g) * kTsluCols + i];
+    }
   }
+  if (t < kTsluRows) s_used[t] = t >= nr;
   __syncthreads();
-  const int nr = s_nr;
   const int steps = min(nr, jb);
   // rows into shared memory, a warp per row (256 contiguous bytes per load instruction),
-  // eight rows' loads in flight before any store; zero past jb and for missing rows
-  constexpr int kWarps = kTsluRows / 32, kBatch = 8;
-  for (int r0 = warp; r0 < kTsluRows; r0 += kWarps * kBatch) {
+  // sixteen rows' loads in flight per warp; zero past jb and for missing rows
+  {
+    constexpr int kWarps = kTsluThreads / 32, kBatch = kTsluRows / kWarps;
     float2 v[kBatch][2];
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
-      const int r = r0 + b * kWarps;
-      const float2* src = A + int64_t(r < nr ? s_rows[r] : 0) * lda;
-      v[b][0] = (r < nr && lane < jb) ? __ldg(src + lane) : make_float2(0.f, 0.f);
-      v[b][1] = (r < nr && lane + 32 < jb) ? __ldg(src + lane + 32) : make_float2(0.f, 0.f);
+      const int rr = warp + b * kWarps;
+      const float2* src = A + int64_t(rr < nr ? s_rows[rr] : 0) * lda;
+      v[b][0] = (rr < nr && lane < jb) ? __ldg(src + lane) : make_float2(0.f, 0.f);
+      v[b][1] = (rr < nr && lane + 32 < jb) ? __ldg(src + lane + 32) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
-      float2* dst = sA + (r0 + b * kWarps) * kTsluLd;
+      float2* dst = sA + (warp + b * kWarps) * kTsluLd;
       dst[lane] = v[b][0];
       dst[lane + 32] = v[b][1];
-      if (lane < kTsluLd - kTsluCols) dst[kTsluCols + lane] = make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
-  bool used = t >= nr;
+  bool used = t >= nr;  // (row threads: warps 0-7)
   int order = -1;
-  float2* my = sA + t * kTsluLd;
+  const int npairs = (jb + 1) >> 1;
   for (int cb = 0; cb < steps; cb += kTsluBlk) {
     const int ce = min(cb + kTsluBlk, steps);  // pivot steps of this block
     const int cbe = min(cb + kTsluBlk, jb);    // columns of this block
-    // the eight steps of the block, each compiled for its position JJ inside the block
-    auto step = [&](auto jj_tag) {
-      constexpr int JJ = decltype(jj_tag)::value;
-      const int j = cb + JJ;
-      if (j >= ce) return;  // the same for every thread
-      // pivot: the largest |Re| + |Im| in column j among unused rows, ties to the lowest row
-      unsigned key = 0;
-      if (!used) {
-        const float2 v = my[j];
-        key = __float_as_uint(fabsf(v.x) + fabsf(v.y));
-      }
-      const unsigned mk = __reduce_max_sync(0xffffffffu, key);
-      const unsigned bal = __ballot_sync(0xffffffffu, !used && key == mk);
-      if (lane == 0)
-        s_wk[warp] = bal ? (static_cast<unsigned long long>(mk) << 32) |
-                               (0xFFFFFFFFu - unsigned(warp * 32 + __ffs(bal) - 1))
-                         : 0ull;
-      __syncthreads();
-      unsigned long long best = s_wk[0];
+    if (warp < kTsluStepWarps) {
+      float4* myb = reinterpret_cast<float4*>(sA + t * kTsluLd + cb);
+      float2 bv[kTsluBlk];
 #pragma unroll
-      for (int w = 1; w < kTsluRows / 32; ++w) best = s_wk[w] > best ? s_wk[w] : best;
-      const int p = int(0xFFFFFFFFu - unsigned(best & 0xFFFFFFFFull));  // an unused row exists: j < nr
-      if (t == p) {
-        used = true;
-        order = j;
+      for (int i = 0; i < kTsluBlk / 2; ++i) {
+        const float4 w = myb[i];
+        bv[2 * i] = make_float2(w.x, w.y);
+        bv[2 * i + 1] = make_float2(w.z, w.w);
       }
-      if (t == 0) s_piv[JJ] = p;
-      if (!used) {  // eliminate column j inside the block (all loads before the stores)
-        constexpr int W = kTsluBlk - JJ;
-        const float2* pr = sA + p * kTsluLd;
-        float2 pu[W], mv[W];
+      // the eight steps of the block, each compiled for its position JJ inside the block
+      auto step = [&](auto jj_tag) {
+        constexpr int JJ = decltype(jj_tag)::value, B = JJ & 1;
+        const int j = cb + JJ;
+        if (j >= ce) return;  // the same for every thread
+        // pivot: the largest |Re| + |Im| in column j among unused rows, compared on the top
+        // 24 bits of its float pattern (15 mantissa bits), ties to the lowest row.  One
+        // 32-bit key per row: bit 31 marks a candidate, the low 8 bits hold 255 - row.
+        const float2 vj = bv[JJ];
+        const unsigned key =
+            used ? 0u
+                 : (0x80000000u | (__float_as_uint(fabsf(vj.x) + fabsf(vj.y)) & 0x7FFFFF00u) | unsigned(255 - t));
+        const float2 myinv = cinv(vj);  // the inverse as pivot, ready before the argmax ends
+        const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+        if (lane == 0) s_wk[B][warp] = mk;
+        if (key == mk && mk != 0u) {  // this warp's candidate (the row bits make it unique)
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-          if (j + q < cbe) {
-            pu[q] = pr[j + q];
-            mv[q] = my[j + q];
+          for (int i = 0; i < kTsluBlk / 2; ++i)
+            s_stage[B][warp][i] = make_float4(bv[2 * i].x, bv[2 * i].y, bv[2 * i + 1].x, bv[2 * i + 1].y);
+          s_inv[B][warp] = myinv;
+        }
+        step_bar();
+        const unsigned g = __reduce_max_sync(0xffffffffu, lane < kTsluStepWarps ? s_wk[B][lane] : 0u);
+        const int p = 255 - int(g & 255u);  // an unused row exists: j < nr
+        if (t == 0) s_piv[JJ] = p;
+        if (t == p) {
+          used = true;
+          order = j;
+          s_used[t] = 1;
+        }
+        if (!used) {  // eliminate column j from my block columns
+          const float4* ps = s_stage[B][p >> 5];
+          const float2 l = cmulf(vj, s_inv[B][p >> 5]);
+          bv[JJ] = l;
+#pragma unroll
+          for (int qq = JJ + 1; qq < kTsluBlk; ++qq) {
+            if (cb + qq < cbe) {
+              const float4 uw = ps[qq >> 1];
+              cfms(bv[qq], l, (qq & 1) ? make_float2(uw.z, uw.w) : make_float2(uw.x, uw.y));
+            }
           }
         }
-        const float2 l = cmulf(mv[0], cinv(pu[0]));
-        my[j] = l;
+      };
+      step(std::integral_constant<int, 0>{});
+      step(std::integral_constant<int, 1>{});
+      step(std::integral_constant<int, 2>{});
+      step(std::integral_constant<int, 3>{});
+      step(std::integral_constant<int, 4>{});
+      step(std::integral_constant<int, 5>{});
+      step(std::integral_constant<int, 6>{});
+      step(std::integral_constant<int, 7>{});
 #pragma unroll
-        for (int q = 1; q < W; ++q) {
-          if (j + q < cbe) {
-            cfms(mv[q], l, pu[q]);
-            my[j + q] = mv[q];
-          }
-        }
-      }
-      __syncthreads();  // column j + 1 is up to date; s_wk may be rewritten
-    };
-    step(std::integral_constant<int, 0>{});
-    step(std::integral_constant<int, 1>{});
-    step(std::integral_constant<int, 2>{});
-    step(std::integral_constant<int, 3>{});
-    step(std::integral_constant<int, 4>{});
-    step(std::integral_constant<int, 5>{});
-    step(std::integral_constant<int, 6>{});
-    step(std::integral_constant<int, 7>{});
-    if (cbe >= jb) continue;
+      for (int i = 0; i < kTsluBlk / 2; ++i)
+        myb[i] = make_float4(bv[2 * i].x, bv[2 * i].y, bv[2 * i + 1].x, bv[2 * i + 1].y);
+    }
+    if (cbe >= jb) continue;  // the same for every thread
     const int npiv = ce - cb;
+    __syncthreads();  // block columns, s_piv and s_used are in shared memory
     // trailing columns of the block's pivot rows: U12 = L11^{-1} A12 (L11 unit lower, the
     // multipliers the pivot rows received inside the block), one thread per column
-    for (int k = cbe + t; k < jb; k += blockDim.x) {
-      for (int i = 0; i < npiv; ++i) {
-        float2* ui = sA + s_piv[i] * kTsluLd;
-        float2 u = ui[k];
-        for (int q = 0; q < i; ++q) cfms(u, ui[cb + q], sA[s_piv[q] * kTsluLd + k]);
-        ui[k] = u;
+    if (t < jb - cbe) {
+      const int k = cbe + t;
+      float2 u[kTsluBlk];
+#pragma unroll
+      for (int i = 0; i < kTsluBlk; ++i) {
+        if (i < npiv) {
+          float2* ui = sA + s_piv[i] * kTsluLd;
+          float2 a = ui[k];
+#pragma unroll
+          for (int qq = 0; qq < i; ++qq) cfms(a, ui[cb + qq], u[qq]);
+          u[i] = a;
+          ui[k] = a;
+        }
       }
     }
     __syncthreads();
-    // rank-npiv update of the rows not chosen yet, two columns per 16-byte access
-    if (!used) {
-      float2 l[kTsluBlk];
-      const float2* pv[kTsluBlk];
+    // rank-npiv update of the rows not chosen yet over their column pairs right of the
+    // block, thread (r, h) taking the pairs P with P % 2 == h
+    {
+      const int r = t >> 1, h = t & 1;
+      if (!s_used[r]) {
+        const float2* my = sA + r * kTsluLd;
+        float2 l[kTsluBlk];
+        const float4* pv[kTsluBlk];
 #pragma unroll
-      for (int q = 0; q < kTsluBlk; ++q) {
-        l[q] = q < npiv ? my[cb + q] : make_float2(0.f, 0.f);
-        pv[q] = sA + s_piv[q < npiv ? q : 0] * kTsluLd;
-      }
-      for (int k = cbe; k < jb; k += 2) {
-        float4 a = *reinterpret_cast<const float4*>(my + k);
-        float4 u[kTsluBlk];
-#pragma unroll
-        for (int q = 0; q < kTsluBlk; ++q)
-          u[q] = q < npiv ? *reinterpret_cast<const float4*>(pv[q] + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < kTsluBlk; ++q) {
-          a.x -= l[q].x * u[q].x - l[q].y * u[q].y;
-          a.y -= l[q].x * u[q].y + l[q].y * u[q].x;
-          a.z -= l[q].x * u[q].z - l[q].y * u[q].w;
-          a.w -= l[q].x * u[q].w + l[q].y * u[q].z;
+        for (int i = 0; i < kTsluBlk; i += 2) {
+          const float4 v = reinterpret_cast<const float4*>(my)[(cb + i) >> 1];
+          l[i] = make_float2(v.x, v.y);
+          l[i + 1] = make_float2(v.z, v.w);
         }
-        *reinterpret_cast<float4*>(my + k) = a;
+#pragma unroll
+        for (int i = 0; i < kTsluBlk; ++i) pv[i] = reinterpret_cast<const float4*>(sA + s_piv[i < npiv ? i : 0] * kTsluLd);
+        float4* myw = reinterpret_cast<float4*>(const_cast<float2*>(my));
+        int P = (cbe >> 1) + h;
+        for (; P + kTsluSub < npairs; P += 2 * kTsluSub) {  // two pairs per pass: more loads in flight
+          float4 a0 = myw[P], a1 = myw[P + kTsluSub];
+          float4 u0[kTsluBlk], u1[kTsluBlk];
+#pragma unroll
+          for (int i = 0; i < kTsluBlk; ++i) {
+            if (i < npiv) {
+              u0[i] = pv[i][P];
+              u1[i] = pv[i][P + kTsluSub];
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kTsluBlk; ++i) {
+            if (i < npiv) {
+              cfms2(a0, l[i], u0[i]);
+              cfms2(a1, l[i], u1[i]);
+            }
+          }
+          myw[P] = a0;
+          myw[P + kTsluSub] = a1;
+        }
+        if (P < npairs) {
+          float4 a = myw[P];
+#pragma unroll
+          for (int i = 0; i < kTsluBlk; ++i)
+            if (i < npiv) cfms2(a, l[i], pv[i][P]);
+          myw[P] = a;
+        }
       }
     }
     __syncthreads();
   }
-  if (order >= 0) {
+  if (order >= 0) {  // a row thread whose row was chosen at step `order`
     out_idx[blockIdx.x * kTsluCols + order] = s_rows[t];
     if (root) {
       sel[order] = s_rows[t];
-      for (int c = 0; c < kTsluCols; ++c) top[order * kTsluCols + c] = my[c];
+      // every value of the row was last written by this thread or before a CTA barrier
+      const float4* src = reinterpret_cast<const float4*>(sA + t * kTsluLd);
+      float4* dst = reinterpret_cast<float4*>(top + order * kTsluCols);
+#pragma unroll 8
+      for (int P = 0; P < kTsluPairs; ++P) dst[P] = src[P];
     }
   }
   if (t == 0) out_cnt[blockIdx.x] = steps;
@@ -236,7 +313,7 @@ __global__ void __launch_bounds__(kTsluRows, 1)
 __global__ void __launch_bounds__(256) tslu_apply_kernel(float2* __restrict__ A, int64_t lda, int jb,
                                                          const int* __restrict__ sel, const float2* __restrict__ top,
                                                          int32_t* __restrict__ ipiv, int64_t row_base,
-                                                         int* __restrict__ status) {
+                                                         int* __restrict__ status, int2* __restrict__ moves) {
   __shared__ int s_sel[kTsluCols];
   __shared__ int s_pos_of[2 * kTsluCols], s_qi_of[2 * kTsluCols];  // per slot: position, index of that position in sel
   __shared__ int s_at[kTsluCols], s_atq[kTsluCols];                // slot at top position p / at position sel[i]
@@ -252,9 +329,11 @@ __global__ void __launch_bounds__(256) tslu_apply_kernel(float2* __restrict__ A,
     s_qi_of[jb + t] = t;
     s_atq[t] = jb + t;
   }
-  for (int e = t; e < jb * kTsluCols; e += blockDim.x) {
-    const int r = e / kTsluCols, c = e % kTsluCols;
-    s_orig[r][c] = c < jb ? A[int64_t(r) * lda + c] : make_float2(0.f, 0.f);
+  // (fixed trip counts: all sixteen loads of a thread are in flight together)
+#pragma unroll
+  for (int k = 0; k < kTsluCols * kTsluCols / 256; ++k) {
+    const int e = t + 256 * k, r = e / kTsluCols, c = e % kTsluCols;
+    s_orig[r][c] = (r < jb && c < jb) ? A[int64_t(r) * lda + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   if (t == 0) {
@@ -281,15 +360,26 @@ __global__ void __launch_bounds__(256) tslu_apply_kernel(float2* __restrict__ A,
     }
   }
   __syncthreads();
-  // positions sel[i] >= jb now hold original top rows (slot < jb)
-  for (int e = t; e < jb * jb; e += blockDim.x) {
-    const int i = e / jb, c = e % jb;
-    const int pos = s_sel[i], slot = s_atq[i];
-    if (pos >= jb && slot >= 0 && slot < jb) A[int64_t(pos) * lda + c] = s_orig[slot][c];
+  // the same permutation as (source, destination) positions for the other columns: position
+  // i takes the row from sel[i]; a displaced original top row goes to its slot's position
+  if (t < jb) {
+    const int pos = s_sel[t], slot = s_atq[t];
+    moves[t] = pos != t ? make_int2(pos, t) : make_int2(-1, -1);
+    moves[jb + t] = (pos >= jb && slot >= 0 && slot < jb) ? make_int2(slot, pos) : make_int2(-1, -1);
   }
-  for (int e = t; e < jb * jb; e += blockDim.x) {
-    const int r = e / jb, c = e % jb;
-    A[int64_t(r) * lda + c] = top[r * kTsluCols + c];
+  // positions sel[i] >= jb now hold original top rows (slot < jb)
+#pragma unroll
+  for (int k = 0; k < kTsluCols * kTsluCols / 256; ++k) {
+    const int e = t + 256 * k, i = e / kTsluCols, c = e % kTsluCols;
+    if (i < jb && c < jb) {
+      const int pos = s_sel[i], slot = s_atq[i];
+      if (pos >= jb && slot >= 0 && slot < jb) A[int64_t(pos) * lda + c] = s_orig[slot][c];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTsluCols * kTsluCols / 256; ++k) {
+    const int e = t + 256 * k, r = e / kTsluCols, c = e % kTsluCols;
+    if (r < jb && c < jb) A[int64_t(r) * lda + c] = top[r * kTsluCols + c];
   }
   if (t < jb) {
     const float2 d = top[t * kTsluCols + t];
@@ -339,6 +429,35 @@ __global__ void __launch_bounds__(256) tslu_lsolve_kernel(float2* __restrict__ A
   }
 }
 
+// The panel's row permutation on the columns outside it (left: earlier L columns; right:
+// the trailing matrix).  Row j0 + dst takes the old values of row j0 + src for every move
+// (at most 2 jb rows, each a source once and a destination once).  A CTA covers 32 columns:
+// lanes run along a row (256-byte accesses), the 8 warps split the moves, and every read of
+// the CTA's columns happens before any write.
+__global__ void __launch_bounds__(256) tslu_swap_kernel(float2* __restrict__ A, int64_t n, int64_t lda, int64_t j0,
+                                                        int jb, const int2* __restrict__ moves) {
+  __shared__ int2 s_mv[2 * kTsluCols];
+  const int t = threadIdx.x;
+  if (t < 2 * jb) s_mv[t] = moves[t];
+  __syncthreads();
+  const int tx = t & 31, ty = t >> 5;
+  const int64_t c = int64_t(blockIdx.x) * 32 + tx;
+  const bool col_ok = c < n && (c < j0 || c >= j0 + jb);
+  constexpr int kPer = 2 * kTsluCols / 8;
+  float2 v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int mi = ty + 8 * k;
+    if (col_ok && mi < 2 * jb && s_mv[mi].x >= 0) v[k] = A[(j0 + s_mv[mi].x) * lda + c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int mi = ty + 8 * k;
+    if (col_ok && mi < 2 * jb && s_mv[mi].x >= 0) A[(j0 + s_mv[mi].y) * lda + c] = v[k];
+  }
+}
+
 inline unsigned cdivu(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
 }  // namespace
@@ -346,7 +465,7 @@ inline unsigned cdivu(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); 
 size_t tslu_scratch_bytes(int64_t n) {
   const int64_t leaves = (n + kTsluRows - 1) / kTsluRows;
   return size_t(2 * leaves * kTsluCols + 2 * leaves + kTsluCols) * sizeof(int) +
-         size_t(kTsluCols * kTsluCols) * sizeof(float2) + 256;
+         size_t(kTsluCols * kTsluCols) * sizeof(float2) + size_t(2 * kTsluCols) * sizeof(int2) + 256;
 }
 
 cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, int64_t row_base, void* scratch,
@@ -357,7 +476,8 @@ cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, 
   const int64_t leaves_max = (n_max + kTsluRows - 1) / kTsluRows;
   char* base = static_cast<char*>(scratch);
   float2* top = reinterpret_cast<float2*>(base);
-  int* idx0 = reinterpret_cast<int*>(top + kTsluCols * kTsluCols);
+  int2* moves = reinterpret_cast<int2*>(top + kTsluCols * kTsluCols);
+  int* idx0 = reinterpret_cast<int*>(moves + 2 * kTsluCols);
   int* idx1 = idx0 + leaves_max * kTsluCols;
   int* cnt0 = idx1 + leaves_max * kTsluCols;
   int* cnt1 = cnt0 + leaves_max;
@@ -374,18 +494,18 @@ cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, 
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  tslu_gepp_kernel<<<groups, kTsluRows, kTsluSmem, s>>>(A, lda, m, jb, nullptr, nullptr, 0, idx0, cnt0, top, sel);
+  tslu_gepp_kernel<<<groups, kTsluThreads, kTsluSmem, s>>>(A, lda, m, jb, nullptr, nullptr, 0, idx0, cnt0, top, sel);
   uint64_t nl = 1;
   int *in_i = idx0, *in_c = cnt0, *out_i = idx1, *out_c = cnt1;
   while (groups > 1) {
     const int next = (groups + kTsluFanIn - 1) / kTsluFanIn;
-    tslu_gepp_kernel<<<next, kTsluRows, kTsluSmem, s>>>(A, lda, m, jb, in_i, in_c, groups, out_i, out_c, top, sel);
+    tslu_gepp_kernel<<<next, kTsluThreads, kTsluSmem, s>>>(A, lda, m, jb, in_i, in_c, groups, out_i, out_c, top, sel);
     ++nl;
     groups = next;
     int* ti = in_i; in_i = out_i; out_i = ti;
     int* tc = in_c; in_c = out_c; out_c = tc;
   }
-  tslu_apply_kernel<<<1, 256, 0, s>>>(A, lda, jb, sel, top, ipiv, row_base, d_status);
+  tslu_apply_kernel<<<1, 256, 0, s>>>(A, lda, jb, sel, top, ipiv, row_base, d_status, moves);
   ++nl;
   if (m > jb) {
     static int nsm[64] = {};
@@ -395,6 +515,13 @@ cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, 
     ++nl;
   }
   return launched(nl);
+}
+
+cudaError_t tslu_swap(void* A, int64_t n, int64_t lda, int64_t j0, int jb, const void* scratch, cudaStream_t s) {
+  if (jb <= 0 || jb > kTsluCols) return cudaErrorInvalidValue;
+  const int2* moves = reinterpret_cast<const int2*>(static_cast<const float2*>(scratch) + kTsluCols * kTsluCols);
+  tslu_swap_kernel<<<cdivu(n, 32), 256, 0, s>>>(static_cast<float2*>(A), n, lda, j0, jb, moves);
+  return launched();
 }
 
 }  // namespace fosb
