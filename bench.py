@@ -58,7 +58,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
 LU_BLOCK = 256  # column block of the complex64 LU: every trailing update has K = 256
 # DRAM bytes (read + write) per complex64 output element of one tcgen05 LU-update launch,
 # from the ncu capture summarised in profiles/ (C is read and written once: 16 B algorithmic)
-LU_UPDATE_DRAM_BYTES_PER_OUTPUT = None
+LU_UPDATE_DRAM_BYTES_PER_OUTPUT = (653.6512e6 + 390.073344e6) / 7424.0**2  # 18.94 B
 
 
 def _peaks():
@@ -245,7 +245,8 @@ def run_fosb(args):
                       "cgemm_update_split_kernel (persistent tcgen05 kind::tf32 N = 256, 3xTF32 complex, operands "
                       "split once per block and bulk-copied; the split kernels are timed with it)",
                       f"TF32 dense = bf16 sustained {bf16} ({bf16_src}) x 1.1/2.25; work = useful complex flops "
-                      "8MNK (3xTF32 executes 3x that on the tensor pipe, so frac <= 1/3)"),
+                      "8MNK; 3xTF32 executes 3x that on the tensor pipe (tensor_pipe_frac: executed TF32 rate / "
+                      "the TF32 MMA rate fosb_peak_microbench measures, which is above the nominal-ratio peak)"),
         "lu_update64": ("tensor", 1.0, tf32_peak,
                         "cgemm_update_tc_ws_kernel (the K = 64 updates inside each 256-column block of the LU)",
                         "work = useful complex flops 8MNK"),
@@ -288,6 +289,8 @@ def run_fosb(args):
         if LU_UPDATE_DRAM_BYTES_PER_OUTPUT is not None:
             roofline["traffic"] = round(LU_UPDATE_DRAM_BYTES_PER_OUTPUT * avg_outputs)
         roofline["algorithmic_bytes"] = round(16.0 * avg_outputs)
+        if upeaks.get("tf32"):
+            roofline["tensor_pipe_frac"] = round(3.0 * achieved / upeaks["tf32"], 4)
     secondary = {}
     for f, (b, wsc, pk, kn, _) in fam_model.items():
         s_ = fam_stats[f]
