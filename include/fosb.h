@@ -218,7 +218,7 @@ fosb_status fosb_lu_destroy(fosb_lu lu);
  * panel kernel in 64-column blocks, and allocates nothing: the panel kernel's scratch lives
  * in a 1 MiB static device array that every GPU loading the library holds until the
  * process exits.  For complex128 these are fosb_factor's pivots and kernels; for complex64
- * fosb_factor uses tournament pivoting in 128-column blocks, so the pivots and factors of
+ * fosb_factor uses tournament pivoting in 256-column blocks, so the pivots and factors of
  * the two calls can differ while the solutions agree to rounding.
  *   A    : device, n x n row-major (lda >= n), complex128 (prec = FOSB_FP64) or complex64
  *          (prec = FOSB_FP32); overwritten by L (unit lower, below the diagonal) and U.

@@ -3,9 +3,10 @@
 //   * gemm: C = alpha op(A) op(B) + beta C, complex128 or complex64.  A 64 x 64 tiled SIMT
 //     kernel for wide products and a row-per-warp kernel for skinny products
 //     (<= 8 right-hand sides), which streams A once at HBM speed (IR residuals).
-//   * getrf: blocked right-looking LU.  complex64 factors: 128-column blocks, each factored
-//     as two 64-column tournament-pivoting panels (tslu.cu), with the tcgen05 3xTF32
-//     trailing update (tc_gemm.cu, K = 128).  complex128 factors: 64-column panels by a
+//   * getrf: blocked right-looking LU.  complex64 factors: 256-column blocks, each factored
+//     as four 64-column tournament-pivoting panels (tslu.cu) with K = 64 updates between
+//     them (tc_gemm.cu), then one tcgen05 3xTF32 trailing update with K = 256 (tc_update.cu,
+//     operands split once per block).  complex128 factors: 64-column panels by a
 //     cooperative partial-pivoting kernel whose CTAs own row chunks and meet at a software
 //     grid barrier once per column (bounded spin: on time-out the status word is set and
 //     the kernel returns), then row swaps, the unit-lower solve of the block row and the
