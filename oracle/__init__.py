@@ -328,6 +328,69 @@ def ct_farfield_covariance(levels: dict, L0: int, L: int, kernel: str, sigma: fl
     return out
 
 
+def pivoted_cholesky(K: np.ndarray, tol: float = 0.0, max_rank: int | None = None):
+    """Pivoted (greedy) Cholesky factorisation K ~ L L^T of a symmetric positive
+    semi-definite matrix: the low-rank factorisation of the tensor equations' right-hand
+    side that Section VI names as further work (Harbrecht, Peters and Schneider 2012).
+    With P the pivots chosen so far, the remainder is the Schur complement
+    S = K - L L^T; each step takes the largest remaining diagonal entry of S (ties to the
+    lowest index) as the next pivot p, appends the column S[:, p] / sqrt(S[p, p]), and
+    the steps stop once trace(S) <= tol * trace(K), no positive diagonal entry is left,
+    or max_rank columns exist.  Returns (L (n x m), pivots (m), trace(S))."""
+    n = K.shape[0]
+    max_rank = n if max_rank is None else min(int(max_rank), n)
+    d = np.array(np.diag(K), dtype=float)
+    trace = d.sum()
+    used = np.zeros(n, dtype=bool)
+    L = np.zeros((n, max_rank))
+    piv = []
+    err = trace
+    m = 0
+    while m < max_rank:
+        cand = np.where(used, -np.inf, d)
+        p = int(np.argmax(cand))
+        if err <= tol * trace or not (cand[p] > 0.0):
+            break
+        lpp = math.sqrt(d[p])
+        col = (K[:, p] - L[:, :m] @ L[p, :m]) / lpp   # column p of the Schur complement / sqrt(pivot)
+        col[used] = 0.0
+        col[p] = lpp
+        L[:, m] = col
+        d = d - col * col
+        used[p] = True
+        d[p] = 0.0
+        piv.append(p)
+        m += 1
+        err = np.where(used, 0.0, np.maximum(d, 0.0)).sum()
+    return L[:, :m], np.array(piv, dtype=np.int64), float(err)
+
+
+def ct_farfield_covariance_lowrank(levels: dict, L0: int, L: int, kernel: str, sigma: float, ell: float,
+                                   tol: float, max_rank: int | None = None, pseudo: bool = False):
+    """The combination-technique far-field covariance (Section IV-B) with the covariance
+    kernel replaced by its pivoted-Cholesky factor over the vertices of all levels
+    L0..L stacked in level order, K ~ R R^T (Section VI): K_{l1,l2} ~ R_l1 R_l2^T, so
+    Sigma_{l1,l2} ~ (Z_l1^{-1} B_l1 R_l1)(Z_l2^{-1} B_l2 R_l2)^H and, with
+    Y_l = A_l Z_l^{-1} B_l R_l, each block's far-field term is Y_l1 Y_l2^H (Y_l1 Y_l2^T for
+    the pseudo-covariance), mirrored when l1 != l2.  Returns (Cov, rank, trace error)."""
+    lv = list(range(L0, L + 1))
+    X = np.vstack([levels[l].mesh.verts for l in lv])
+    R, _, err = pivoted_cholesky(cov_kernel(X, X, kernel, sigma, ell), tol, max_rank)
+    Y, off = {}, 0
+    for l in lv:
+        a = levels[l]
+        V = a.mesh.verts.shape[0]
+        Y[l] = a.A @ np.linalg.solve(a.Z, a.B @ R[off:off + V])
+        off += V
+    out = None
+    for (l1, l2), sgn in ct_hermitian_blocks(L0, L):
+        M = Y[l1] @ (Y[l2].T if pseudo else Y[l2].conj().T)
+        if l1 != l2:
+            M = M + (M.T if pseudo else M.conj().T)
+        out = sgn * M if out is None else out + sgn * M
+    return out, R.shape[1], err
+
+
 def rcs_variance_db(F: np.ndarray, cov: np.ndarray, pcov: np.ndarray) -> np.ndarray:
     """Delta-method variance of RCS_dB = 10 log10(|F|^2/(4 pi)) at each direction:
     Var = (20/ln 10)^2 Var[Re(conj F . F')]/|F|^4 with Var[Re z] = (E|z|^2 + Re E[z^2])/2,
