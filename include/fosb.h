@@ -269,6 +269,47 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
                                   const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
                                   int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream);
 
+/* ---- Low-rank right-hand side of the tensor equations (Section VI, further work (ii)) ----
+ * fosb_kernel_lowrank: pivoted Cholesky factorisation K ~ R^T R (Harbrecht, Peters and
+ * Schneider 2012) of the covariance kernel matrix K_pq = sigma^2 rho(|x_p - x_q|) over the
+ * vertices of nmesh meshes stacked in order (mesh i's vertices follow those of meshes
+ * 0..i-1), so that for two of them K_12 ~ R_1^T R_2 with R_i the columns of mesh i.  Step m
+ * takes as pivot the point with the largest diagonal entry of the remainder K - R^T R among
+ * those not chosen yet (ties to the lowest index) and appends that remainder's column
+ * divided by the square root of the pivot; the steps stop once the remainder's trace is
+ * at most tol * trace(K) (trace(K) = V sigma^2), when no positive diagonal entry is left,
+ * or after max_rank columns.  Kernel values are computed on the fly in FP64.
+ *   meshes    : nmesh handles (host array)
+ *   R         : device, max_rank x ldr float64 row-major (ldr >= total vertices V); row m is
+ *               column m of the factor; rows >= *rank are left untouched
+ *   rank      : host out, the number of columns written
+ *   trace_err : host out (may be NULL), the trace of K - R^T R with *rank columns
+ * Synchronises `stream` (the host checks the stopping rule every 32 columns).
+ * Errors: FOSB_ERR_INVALID_ARG (bad kernel, tol < 0, max_rank < 1, ldr < V).
+ *
+ * fosb_covariance_lowrank: for one level, Y = A Z^{-1} B R_l^T (3 n_dir x r): the factor of
+ * the far-field covariance under K ~ R^T R, since then
+ *   A_1 Sigma_12 A_2^H ~ (A_1 Z_1^{-1} B_1 R_1^T)(A_2 Z_2^{-1} B_2 R_2^T)^H = Y_1 Y_2^H
+ * (B, A and the refined solve as in fosb_covariance and fosb_farfield_moments).
+ *   u   : device nominal current of this level; R : device r x V_l float64 (ldr >= V_l),
+ *         the mesh's columns of the factor (a pointer into fosb_kernel_lowrank's R)
+ *   Y   : device 3 n_dir x r row-major (ldy >= r), complex128 (FP64/MIXED factors) or
+ *         complex64 (FP32), overwritten.  Synchronises `stream` (refinement).
+ * fosb_lowrank_combine: out = (accumulate ? out : 0) + weight (M [+ op(M)]) with
+ *   M = Y1 op(Y2), op = ^H (pseudo = 0) or ^T (pseudo = 1, the pseudo-covariance), the mirror
+ *   added when hermitian_mirror = 1 (a block with l1 != l2 of the CT sum, Section IV-B).
+ *   Y1, Y2 : device nd3 x r (ldy1, ldy2 >= r); out : device nd3 x nd3 (ldo >= nd3).
+ *   Enqueued on `stream`. */
+fosb_status fosb_kernel_lowrank(const fosb_mesh* meshes, int64_t nmesh, const fosb_cov_kernel* kernel, double tol,
+                                int64_t max_rank, double* R, int64_t ldr, int64_t* rank, double* trace_err,
+                                void* stream);
+fosb_status fosb_covariance_lowrank(fosb_mesh mesh, fosb_lu lu, const void* u, double k, const double* R, int64_t ldr,
+                                    int64_t r, const double* dirs, int64_t n_dir, const fosb_refine_opts* ropt,
+                                    void* Y, int64_t ldy, void* stream);
+fosb_status fosb_lowrank_combine(int64_t nd3, int64_t r, const void* Y1, int64_t ldy1, const void* Y2, int64_t ldy2,
+                                 double weight, int hermitian_mirror, int pseudo, int prec, void* out, int64_t ldo,
+                                 int accumulate, void* stream);
+
 /* ---- A11: RCS mean and variance per direction ---------------------------------------
  * From the moments of fosb_farfield_moments, for every observation direction d (mean far
  * field f = F_d, 3 x 3 blocks C = Cov[F'_d] and P = E[F'_d F'_d^T] of the covariance and

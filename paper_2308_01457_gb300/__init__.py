@@ -75,7 +75,8 @@ def lib():
                      "fosb_getrf_static", "fosb_profile_enable", "fosb_profile_read", "fosb_rcs_moments",
                      "fosb_debug_set_wait_limit", "fosb_peak_microbench", "fosb_assemble_efie_batched",
                      "fosb_solve_batched", "fosb_field_samples", "fosb_mesh_perturb", "fosb_mc_moments",
-                     "fosb_zgemm_fp64class"):
+                     "fosb_zgemm_fp64class", "fosb_kernel_lowrank", "fosb_covariance_lowrank",
+                     "fosb_lowrank_combine"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -221,6 +222,61 @@ def covariance(m1: Mesh, lu1: LU, u1, m2: Mesh, lu2: LU, u2, k: float, Sigma, ki
                                  ctypes.byref(ker), ctypes.c_int(int(pseudo)), _ptr(Sigma), ctypes.c_int64(_ld(Sigma)),
                                  ctypes.byref(ro), _stream(stream)))
     return Sigma
+
+
+def kernel_lowrank(meshes, kind: int = COV_GAUSS, sigma: float = 1.0, ell: float = 1.0, tol: float = 1e-10,
+                   max_rank: int | None = None, device="cuda:0", stream=None):
+    """fosb_kernel_lowrank: pivoted Cholesky K ~ R^T R of the covariance kernel over the
+    vertices of `meshes` stacked in order.  Returns (R (rank x V float64, device; the
+    columns of mesh i are R[:, off_i:off_i + nv_i]), rank, trace error, offsets)."""
+    import torch
+
+    meshes = list(meshes)
+    V = sum(m.nv for m in meshes)
+    max_rank = V if max_rank is None else min(int(max_rank), V)
+    R = torch.zeros((max_rank, V), dtype=torch.float64, device=device)
+    arr = (ctypes.c_void_p * len(meshes))(*[m.handle.value if isinstance(m.handle, ctypes.c_void_p) else m.handle
+                                            for m in meshes])
+    rank, err = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().fosb_kernel_lowrank(arr, ctypes.c_int64(len(meshes)), ctypes.byref(CovKernel(kind, sigma, ell)),
+                                     ctypes.c_double(tol), ctypes.c_int64(max_rank), _ptr(R), ctypes.c_int64(V),
+                                     ctypes.byref(rank), ctypes.byref(err), _stream(stream)))
+    offs, o = [], 0
+    for m in meshes:
+        offs.append(o)
+        o += m.nv
+    return R[:rank.value], rank.value, err.value, offs
+
+
+def covariance_lowrank(mesh: Mesh, lu: LU, u, k: float, R, dirs, Y=None, max_iters: int = 10, tol: float = 0.0,
+                       stream=None):
+    """fosb_covariance_lowrank: Y = A Z^{-1} B R^T (3 n_dir x r) for one level; R is the
+    level's columns of the kernel factor (r x V_l view of kernel_lowrank's R)."""
+    import torch
+
+    d = _np(dirs, np.float64).reshape(-1, 3)
+    r = R.shape[0]
+    if Y is None:
+        dt = torch.complex64 if lu.prec == FP32 else torch.complex128
+        Y = torch.empty((3 * d.shape[0], r), dtype=dt, device=R.device)
+    ro = RefineOpts(max_iters, tol)
+    _check(lib().fosb_covariance_lowrank(mesh.handle, lu.handle, _ptr(u), ctypes.c_double(k), _ptr(R),
+                                         ctypes.c_int64(R.stride(0)), ctypes.c_int64(r),
+                                         d.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(d.shape[0]),
+                                         ctypes.byref(ro), _ptr(Y), ctypes.c_int64(_ld(Y)), _stream(stream)))
+    return Y
+
+
+def lowrank_combine(Y1, Y2, out, weight: float = 1.0, mirror: bool = False, pseudo: bool = False,
+                    accumulate: bool = False, prec: int | None = None, stream=None):
+    """fosb_lowrank_combine: out (+)= weight (Y1 op(Y2) [+ its op]), op = ^H or ^T (pseudo)."""
+    prec = _prec_of(Y1) if prec is None else prec
+    _check(lib().fosb_lowrank_combine(ctypes.c_int64(Y1.shape[0]), ctypes.c_int64(Y1.shape[1]), _ptr(Y1),
+                                      ctypes.c_int64(_ld(Y1)), _ptr(Y2), ctypes.c_int64(_ld(Y2)),
+                                      ctypes.c_double(weight), ctypes.c_int(int(mirror)), ctypes.c_int(int(pseudo)),
+                                      ctypes.c_int(prec), _ptr(out), ctypes.c_int64(_ld(out)),
+                                      ctypes.c_int(int(accumulate)), _stream(stream)))
+    return out
 
 
 def farfield_moments(m1: Mesh, k: float, dirs, X, out, m2: Mesh | None = None, weight: float = 1.0,

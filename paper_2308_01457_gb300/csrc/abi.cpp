@@ -473,6 +473,88 @@ fosb_status fosb_covariance(fosb_mesh m1, fosb_lu lu1, const void* u1, fosb_mesh
   return FOSB_OK;
 }
 
+fosb_status fosb_kernel_lowrank(const fosb_mesh* meshes, int64_t nmesh, const fosb_cov_kernel* kernel, double tol,
+                                int64_t max_rank, double* R, int64_t ldr, int64_t* rank, double* trace_err,
+                                void* stream) {
+  if (!meshes || nmesh < 1 || !kernel || !R || !rank) return fail(FOSB_ERR_INVALID_ARG, "fosb_kernel_lowrank: NULL argument");
+  if ((kernel->kind != FOSB_COV_GAUSS && kernel->kind != FOSB_COV_MATERN32) || !(kernel->sigma > 0) ||
+      !(kernel->ell > 0) || !std::isfinite(kernel->sigma) || !std::isfinite(kernel->ell))
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_kernel_lowrank: bad covariance kernel");
+  if (!(tol >= 0) || !std::isfinite(tol) || max_rank < 1) return fail(FOSB_ERR_INVALID_ARG, "fosb_kernel_lowrank: tol < 0 or max_rank < 1");
+  std::vector<double> x;
+  for (int64_t i = 0; i < nmesh; ++i) {
+    if (!meshes[i]) return fail(FOSB_ERR_INVALID_ARG, "fosb_kernel_lowrank: NULL mesh");
+    x.insert(x.end(), meshes[i]->verts.begin(), meshes[i]->verts.end());
+  }
+  const int64_t n = int64_t(x.size() / 3);
+  if (ldr < n) return fail(FOSB_ERR_INVALID_ARG, "fosb_kernel_lowrank: ldr < total vertices");
+  max_rank = std::min(max_rank, n);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Scratch dx(s);
+  FOSB_CUDA(dx.alloc(sizeof(double) * x.size()));
+  FOSB_CUDA(cudaMemcpyAsync(dx.p, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice, s));
+  FOSB_TRY(pivoted_cholesky_kernel(dx.as<double>(), n, *kernel, tol, max_rank, R, ldr, rank, trace_err, s));
+  return FOSB_OK;
+}
+
+namespace {
+cudaError_t gemm_prec(int prec, int opA, int opB, int64_t M, int64_t N, int64_t K, double ar, const void* A, int64_t lda,
+                      const void* B, int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s) {
+  if (is_c64(prec)) return gemm<float>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+  if (prec == FOSB_MIXED) return gemm_c128_ff(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+  return gemm<double>(opA, opB, M, N, K, ar, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+}
+}  // namespace
+
+fosb_status fosb_covariance_lowrank(fosb_mesh mesh, fosb_lu lu, const void* u, double k, const double* R, int64_t ldr,
+                                    int64_t r, const double* dirs, int64_t n_dir, const fosb_refine_opts* ropt,
+                                    void* Y, int64_t ldy, void* stream) {
+  if (!mesh || !lu || !u || !R || !dirs || !Y) return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance_lowrank: NULL argument");
+  if (lu->n != mesh->d.ne) return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance_lowrank: factor size != mesh edges");
+  if (r < 1 || ldr < mesh->d.nv || n_dir < 1 || ldy < r || !(k > 0))
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_covariance_lowrank: bad size, leading dimension or k");
+  FOSB_TRY(ensure_rules(5));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int prec = lu->prec;
+  const bool c64 = is_c64(prec);
+  const size_t elem = c64 ? 8 : 16;
+  const DevMesh& d = mesh->d;
+  const int64_t N = d.ne, nd3 = 3 * n_dir;
+  Scratch bell(s), w(s), ddirs(s), a(s);
+  FOSB_CUDA(bell.alloc(sizeof(double) * 8 * N));
+  FOSB_CUDA(launch_sd_rhs(d, k, u, c64, bell.as<double>(), s));
+  FOSB_CUDA(w.alloc(elem * N * r));
+  FOSB_CUDA(launch_br_product(d, bell.as<double>(), R, ldr, r, c64, w.p, r, s));
+  FOSB_TRY(solve_internal(lu, w.p, r, r, w.p, r, ropt, nullptr, s));
+  FOSB_CUDA(ddirs.alloc(sizeof(double) * 3 * n_dir));
+  FOSB_CUDA(cudaMemcpyAsync(ddirs.p, dirs, sizeof(double) * 3 * n_dir, cudaMemcpyHostToDevice, s));
+  FOSB_CUDA(a.alloc(elem * nd3 * N));
+  FOSB_CUDA(cudaMemsetAsync(a.p, 0, elem * nd3 * N, s));
+  FOSB_CUDA(launch_farfield_matrix(d, k, ddirs.as<double>(), n_dir, c64, a.p, s));
+  FOSB_CUDA(gemm_prec(prec, OP_N, OP_N, nd3, r, N, 1.0, a.p, N, w.p, r, 0.0, Y, ldy, s));
+  FOSB_CUDA(cudaStreamSynchronize(s));
+  return FOSB_OK;
+}
+
+fosb_status fosb_lowrank_combine(int64_t nd3, int64_t r, const void* Y1, int64_t ldy1, const void* Y2, int64_t ldy2,
+                                 double weight, int hermitian_mirror, int pseudo, int prec, void* out, int64_t ldo,
+                                 int accumulate, void* stream) {
+  if (!Y1 || !Y2 || !out || nd3 < 1 || r < 1 || ldy1 < r || ldy2 < r || ldo < nd3)
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_lowrank_combine: bad argument");
+  FOSB_TRY(check_prec(prec));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int op = pseudo ? OP_T : OP_C;
+  if (!hermitian_mirror) {
+    FOSB_CUDA(gemm_prec(prec, OP_N, op, nd3, nd3, r, weight, Y1, ldy1, Y2, ldy2, accumulate ? 1.0 : 0.0, out, ldo, s));
+    return FOSB_OK;
+  }
+  Scratch mm(s);
+  FOSB_CUDA(mm.alloc((is_c64(prec) ? 8 : 16) * nd3 * nd3));
+  FOSB_CUDA(gemm_prec(prec, OP_N, op, nd3, nd3, r, 1.0, Y1, ldy1, Y2, ldy2, 0.0, mm.p, nd3, s));
+  FOSB_CUDA(add_mirrored(mm.p, nd3, nd3, op, weight, accumulate != 0, is_c64(prec), out, ldo, s));
+  return FOSB_OK;
+}
+
 fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const double* dirs, int64_t n_dir,
                                   const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
                                   int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream) {

@@ -172,6 +172,13 @@ cudaError_t launch_farfield_matrix(const DevMesh& m, double k, const double* d_d
 // Shape-derivative RHS in ELL form (N x 4 complex128 values on the columns ell_cols),
 // its dense expansion (N x V), and W = B1 K12 (N1 x V2) with K evaluated on the fly.
 cudaError_t launch_sd_rhs(const DevMesh& m, double k, const void* u, bool u_fp32, double* B_ell, cudaStream_t s);
+// Low-rank kernel factor (lowrank.cu): pivoted Cholesky of the covariance kernel matrix over
+// n device points d_x (n x 3), R rows = factor columns; and W (N x r) = B R^T for one mesh.
+fosb_status pivoted_cholesky_kernel(const double* d_x, int64_t n, const fosb_cov_kernel& ker, double tol,
+                                    int64_t max_rank, double* R, int64_t ldr, int64_t* rank, double* trace_err,
+                                    cudaStream_t s);
+cudaError_t launch_br_product(const DevMesh& m, const double* B_ell, const double* R, int64_t ldr, int64_t r, bool fp32,
+                              void* W, int64_t ldw, cudaStream_t s);
 cudaError_t launch_ell_to_dense(const DevMesh& m, const double* B_ell, bool conj_out, bool fp32, void* B, int64_t ldb,
                                 cudaStream_t s);
 cudaError_t launch_bk_product(const DevMesh& m1, const double* B1_ell, const DevMesh& m2,

@@ -10,8 +10,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (ASM_FP64, COV_GAUSS, FP32, MIXED, assemble_efie, covariance, factor, farfield_moments, incidence,
-               mesh_create, rcs_moments, solve)
+from . import (ASM_FP64, COV_GAUSS, FP32, MIXED, assemble_efie, covariance, covariance_lowrank, factor,
+               farfield_moments, incidence, kernel_lowrank, lowrank_combine, mesh_create, rcs_moments, solve)
 
 
 def index_sets(L0: int, L: int):
@@ -67,6 +67,11 @@ class FOSBProblem:
     arith: int = ASM_FP64
     n_ss: int = 5
     pseudo: bool = False
+    # low-rank right-hand side (Section VI): None solves every CT block with fosb_covariance;
+    # a tolerance factors the kernel over all levels' vertices by pivoted Cholesky to that
+    # relative trace error and forms each block as Y_l1 Y_l2^H (fosb_covariance_lowrank)
+    lowrank_tol: float | None = None
+    max_rank: int | None = None
     levels: dict = field(default_factory=dict)
 
     def setup(self, device="cuda:0"):
@@ -133,19 +138,10 @@ class FOSBProblem:
         farfield_moments(fine.mesh, self.k, self.dirs, fine.u, F, prec=self.prec)
         cov = torch.empty((nd3, nd3), dtype=dt, device=dev)
         pcov = torch.empty((nd3, nd3), dtype=dt, device=dev) if self.pseudo else None
-        first = True
-        for (l1, l2), sgn in hermitian_blocks(self.L0, self.L):
-            a, c = self.levels[l1], self.levels[l2]
-            for pseudo, out in ((False, cov), (True, pcov)):
-                if out is None:
-                    continue
-                Sig = torch.empty((a.mesh.n_edges, c.mesh.n_edges), dtype=dt, device=dev)
-                covariance(a.mesh, a.lu, a.u, c.mesh, c.lu, c.u, self.k, Sig, self.kernel, self.sigma, self.ell,
-                           pseudo=pseudo)
-                farfield_moments(a.mesh, self.k, self.dirs, Sig, out, m2=c.mesh, weight=float(sgn), mirror=(l1 != l2),
-                                 prec=self.prec,
-                                 pseudo=pseudo, accumulate=not first)
-            first = False
+        if self.lowrank_tol is not None:
+            self._lowrank_blocks(cov, pcov)
+        else:
+            self._full_blocks(cov, pcov)
         # A11: RCS_dB of the mean field and the variance of every far-field component; with the
         # pseudo-covariance also the delta-method variance of RCS_dB (device float64 tensors)
         n_dir = self.dirs.shape[0]
@@ -158,6 +154,44 @@ class FOSBProblem:
             cov_end.record()
             timers.setdefault("covariance_ct", []).append((cov_start, cov_end))
         return (F, cov) if pcov is None else (F, cov, pcov)
+
+    def _full_blocks(self, cov, pcov):
+        """CT sum over the Hermitian blocks, each Sigma_{l1,l2} from fosb_covariance and
+        projected by fosb_farfield_moments (mirrored when l1 != l2)."""
+        import torch
+
+        first = True
+        for (l1, l2), sgn in hermitian_blocks(self.L0, self.L):
+            a, c = self.levels[l1], self.levels[l2]
+            for pseudo, out in ((False, cov), (True, pcov)):
+                if out is None:
+                    continue
+                Sig = torch.empty((a.mesh.n_edges, c.mesh.n_edges), dtype=cov.dtype, device=cov.device)
+                covariance(a.mesh, a.lu, a.u, c.mesh, c.lu, c.u, self.k, Sig, self.kernel, self.sigma, self.ell,
+                           pseudo=pseudo)
+                farfield_moments(a.mesh, self.k, self.dirs, Sig, out, m2=c.mesh, weight=float(sgn), mirror=(l1 != l2),
+                                 prec=self.prec, pseudo=pseudo, accumulate=not first)
+            first = False
+
+    def _lowrank_blocks(self, cov, pcov):
+        """CT sum with the kernel factor K ~ R^T R over the vertices of levels L0..L:
+        Y_l = A_l Z_l^{-1} B_l R_l^T once per level, then Y_l1 Y_l2^H (and Y_l1 Y_l2^T for the
+        pseudo-covariance) per block.  Sets self.rank and self.trace_err."""
+        lv = list(range(self.L0, self.L + 1))
+        dev = self.levels[self.L].Z.device
+        R, self.rank, self.trace_err, offs = kernel_lowrank([self.levels[l].mesh for l in lv], self.kernel, self.sigma,
+                                                            self.ell, self.lowrank_tol, self.max_rank, device=dev)
+        Y = {}
+        for l, off in zip(lv, offs):
+            st = self.levels[l]
+            Y[l] = covariance_lowrank(st.mesh, st.lu, st.u, self.k, R[:, off:off + st.mesh.nv], self.dirs)
+        first = True
+        for (l1, l2), sgn in hermitian_blocks(self.L0, self.L):
+            for pseudo, out in ((False, cov), (True, pcov)):
+                if out is not None:
+                    lowrank_combine(Y[l1], Y[l2], out, weight=float(sgn), mirror=(l1 != l2), pseudo=pseudo,
+                                    accumulate=not first, prec=self.prec)
+            first = False
 
     def release(self):
         for st in self.levels.values():
