@@ -52,6 +52,13 @@ WORKLOADS = {
     # l = 0.3), of the 1280-triangle sphere (N = 1920), k = 4, d = +z, p = x, 181 H-plane angles
     "mc-sphere-ka4-N1920-M512": dict(kind="mc", level=3, nsamp=512, k=4.0, sigma=0.005, ell=0.3, n_dir=181,
                                      d=(0, 0, 1), p=(1, 0, 0), seed=230801457),
+    # low-rank right-hand side (Section VI): the full tensor of one level (L0 = L = 3: the
+    # 5120-triangle sphere, N = 7680, V = 2562), k = 4, Gaussian sigma = 0.005, l = 0.3, 181
+    # H-plane angles; the kernel factored by pivoted Cholesky to a relative trace error of
+    # 1e-10, timed against the full path (V right-hand sides) on the same problem
+    "lowrank-sphere-ka4-full-L3": dict(kind="lowrank", mesh="sphere", levels=[3], k=4.0, sigma=0.005, ell=0.3,
+                                       n_dir=181, L0=3, L=3, d=(0, 0, 1), p=(1, 0, 0), dirs="hplane",
+                                       kernel="gauss", tol=1e-10),
 }
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
@@ -556,6 +563,96 @@ def run_mc(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lowrank(args):
+    """The low-rank workload: one step = the FOSB step of fosb.ct with the kernel factored by
+    pivoted Cholesky (fosb_kernel_lowrank) and the covariance formed as Y Y^H
+    (fosb_covariance_lowrank, fosb_lowrank_combine).  Outside the timed region the same step
+    on the full path (fosb_covariance with V right-hand sides) gives the comparison time and
+    the difference of the two covariances."""
+    import torch
+
+    import paper_2308_01457_gb300 as F
+
+    F.build.build()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    meshes, dirs = _meshes(W), _dirs(W)
+    arith = F.ASM_FF if args.arith == "ff" else F.ASM_FP64
+
+    def problem(tol):
+        prob = _problem(F, W, meshes, dirs, F.MIXED, arith)
+        prob.pseudo, prob.lowrank_tol = True, tol
+        return prob
+
+    def timed(prob, steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record()
+        for i in range(steps):
+            out = prob.run()
+            prob.release()
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[-1]) / steps, out
+
+    prob = problem(W["tol"])
+    for _ in range(args.warmup):
+        prob.run()
+        prob.release()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = F.lib().fosb_kernel_launches()
+    clocks = _clock_sampler(local) if rank == 0 else None
+    ms, out = timed(prob, args.steps)
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = _clock_summary(clocks)
+    launches = int(F.lib().fosb_kernel_launches() - launches0)
+    ms = _max_over_ranks(ms, ws, "cuda")
+    if rank != 0:
+        return
+    cov_lr, pcov_lr = out[1].cpu().numpy(), out[2].cpu().numpy()
+    full = problem(None)
+    full.run()
+    full.release()
+    ms_full, out_f = timed(full, 1)
+    cov_f, pcov_f = out_f[1].cpu().numpy(), out_f[2].cpu().numpy()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    L = W["L"]
+    V = prob.levels[L].mesh.nv
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per FOSB step", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: float-float regular pairs, f64 singular pairs, 3xTF32 LU with FP64-class refinement, "
+                     "f64 pivoted Cholesky", "data": "synthetic",
+            "config": {"workload": args.workload, "N": prob.levels[L].mesh.n_edges, "V": V, "k": W["k"],
+                       "n_dir": W["n_dir"], "sigma": W["sigma"], "ell": W["ell"], "tol": W["tol"],
+                       "parallelism": f"replicas{ws}"},
+            "rank": prob.rank, "trace_err_rel": prob.trace_err / (V * W["sigma"] ** 2),
+            "full_path": {"s_per_step": round(ms_full / 1e3, 4), "rhs": V,
+                          "rel_diff_cov": rel(cov_lr, cov_f), "rel_diff_pcov": rel(pcov_lr, pcov_f)},
+            "speedup_vs_full_path": round(ms_full / ms, 3), "gpu_launches": launches, "clocks": clk}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        t = time.perf_counter()
+        lev = {L: O.nominal_level(O.from_synth(meshes[0]), W["k"], W["d"], W["p"], dirs)}
+        O.ct_farfield_covariance_lowrank(lev, L, L, W["kernel"], W["sigma"], W["ell"], W["tol"])
+        O.ct_farfield_covariance_lowrank(lev, L, L, W["kernel"], W["sigma"], W["ell"], W["tol"], pseudo=True)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": round(dt, 2), "unit": "s per FOSB step", "cores": len(os.sched_getaffinity(0)),
+                                "kind": "oracle",
+                                "sample": "the complete step: oracle assembly, LAPACK solve, maps and the low-rank "
+                                          "covariance and pseudo-covariance (each with its own pivoted Cholesky)"}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batched(W):
     """The FP64 CPU oracle, as it stands, on the batched workload: assembly, plane-wave
     right-hand sides and the LAPACK solve of all 16 directions, measured for every
@@ -871,15 +968,17 @@ def main():
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     kind = WORKLOADS[args.workload].get("kind")
     if args.impl == "reference":
-        if kind == "mc":
+        if kind in ("mc", "lowrank"):
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the default workload; "
-                              "the Monte Carlo workload reports its oracle baseline in its own line"}))
+                              "this workload reports its oracle baseline in its own line"}))
         else:
             run_reference_batched(args) if kind == "batched" else run_reference(args)
     elif kind == "batched":
         run_batched(args)
     elif kind == "mc":
         run_mc(args)
+    elif kind == "lowrank":
+        run_lowrank(args)
     else:
         run_fosb(args)
 
