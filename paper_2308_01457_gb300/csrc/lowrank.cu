@@ -10,8 +10,9 @@
 //      Schur complement K - R^T R); stop if err <= tol trace(K) or no positive d is left;
 //      otherwise p = argmax of d over those points (ties to the lowest index), l = sqrt(d_p),
 //      and p is marked chosen;
-//   2. a thread per point j: R_m[j] = (K_jp - sum_{k<m} R_k[j] R_k[p]) / l, with l at j = p
-//      and 0 at points chosen earlier; d_j -= R_m[j]^2.
+//   2. per point j (32 points per CTA, the dot product split over its 8 warps):
+//      R_m[j] = (K_jp - sum_{k<m} R_k[j] R_k[p]) / l, with l at j = p and 0 at points chosen
+//      earlier; d_j -= R_m[j]^2.
 // The host launches the steps in groups of 32 and reads the stop flag after each group, so
 // no kernel waits on another.
 #include <cuda_runtime.h>
@@ -31,7 +32,8 @@ struct LrState {
 };
 
 constexpr int kPivThreads = 1024;
-constexpr int kColThreads = 256;
+constexpr int kColGroups = 8;                 // warps per CTA of the column kernel
+constexpr int kColThreads = 32 * kColGroups;  // 32 points per CTA
 constexpr int kStage = 1024;  // R_k[p] values staged per pass
 
 __device__ __forceinline__ double lr_kernel(int kind, double s2, double ell, const double* __restrict__ x, int64_t i,
@@ -111,7 +113,9 @@ __global__ void __launch_bounds__(kPivThreads) lr_pivot_kernel(int64_t n, double
   }
 }
 
-// Step m, part 2: column m of the factor and the diagonal update, a thread per point.
+// Step m, part 2: column m of the factor and the diagonal update.  A CTA takes 32 points
+// (lanes) and splits the dot product with the earlier columns over 8 warps (k = ty mod 8);
+// the 8 partial sums are added in a fixed order by warp 0, which finishes the column.
 __global__ void __launch_bounds__(kColThreads) lr_column_kernel(int64_t n, int kind, double s2, double ell,
                                                                 const double* __restrict__ x, double* d,
                                                                 const unsigned char* chosen, const int* piv,
@@ -119,9 +123,11 @@ __global__ void __launch_bounds__(kColThreads) lr_column_kernel(int64_t n, int k
                                                                 const LrState* st) {
   if (st->rank <= m) return;  // the stopping rule fired at this step or earlier
   __shared__ double s_rp[kStage];
+  __shared__ double s_part[kColGroups][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int p = piv[m];
   const double l = lp[m];
-  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t j = int64_t(blockIdx.x) * 32 + tx;
   double acc = 0.0;
   for (int k0 = 0; k0 < m; k0 += kStage) {
     const int kn = min(kStage, m - k0);
@@ -129,9 +135,14 @@ __global__ void __launch_bounds__(kColThreads) lr_column_kernel(int64_t n, int k
     for (int i = threadIdx.x; i < kn; i += blockDim.x) s_rp[i] = R[int64_t(k0 + i) * ldr + p];
     __syncthreads();
     if (j < n)
-      for (int k = 0; k < kn; ++k) acc += R[int64_t(k0 + k) * ldr + j] * s_rp[k];
+      for (int k = ty; k < kn; k += kColGroups) acc += R[int64_t(k0 + k) * ldr + j] * s_rp[k];
   }
-  if (j >= n) return;
+  s_part[ty][tx] = acc;
+  __syncthreads();
+  if (ty != 0 || j >= n) return;
+  acc = 0.0;
+#pragma unroll
+  for (int g = 0; g < kColGroups; ++g) acc += s_part[g][tx];
   double v;
   if (j == p) {
     v = l;
@@ -183,7 +194,7 @@ fosb_status pivoted_cholesky_kernel(const double* d_x, int64_t n, const fosb_cov
                                                    static_cast<unsigned char*>(ch.p), st);
   FOSB_CUDA(launched());
   LrState h{};
-  const unsigned gcol = lr_blocks(n, kColThreads);
+  const unsigned gcol = lr_blocks(n, 32);
   for (int64_t m0 = 0; m0 < max_rank; m0 += 32) {
     const int64_t m1 = std::min<int64_t>(max_rank, m0 + 32);
     for (int64_t m = m0; m < m1; ++m) {
