@@ -172,12 +172,16 @@ fosb_status fosb_mesh_destroy(fosb_mesh mesh);
  *   Z       : device, N x N, row-major, leading dimension ldz >= N; overwritten
  *   inc     : host, n_inc x 9 float64: d (3, unit), Re p (3), Im p (3); may be NULL if n_inc = 0
  *   b       : device, N x n_inc (leading dimension ldb >= n_inc), same complex type as Z; may be NULL
+ * Enqueued on `stream` without synchronising it; `inc` may be reused once the call returns.
  * Errors: FOSB_ERR_INVALID_ARG. */
 fosb_status fosb_assemble_efie(fosb_mesh mesh, double k, const fosb_quad_opts* opts, int prec, void* Z, int64_t ldz,
                                const double* inc, int64_t n_inc, void* b, int64_t ldb, void* stream);
 
 /* ---- A5: LU factorisation -----------------------------------------------------------
- * P Z = L U with partial pivoting (largest |Re| + |Im|, ties to the lowest row).
+ * P Z = L U.  complex128 factors (FOSB_FP64): partial pivoting (largest |Re| + |Im|, ties to
+ * the lowest row).  complex64 factors (FOSB_MIXED, FOSB_FP32): 256-column blocks of 64-column
+ * panels whose pivot rows a tournament chooses (leaves of 256 rows and a fan-in-4 tree, each
+ * choosing by partial pivoting with the magnitudes compared on their top 15 mantissa bits).
  *   Z    : device, n x n row-major (complex128 for FP64/MIXED, complex64 for FP32);
  *          read, not modified.  For FOSB_MIXED the handle keeps a NON-owning reference
  *          to Z for the FP64 residuals: Z must stay alive and unchanged until

@@ -309,12 +309,14 @@ fosb_status fosb_assemble_efie(fosb_mesh mesh, double k, const fosb_quad_opts* o
   FOSB_CUDA(launch_assemble_regular(mesh->d, k, arith, Z, ldz, s));
   FOSB_CUDA(launch_assemble_singular(mesh->d, k, nss, is_c64(prec), Z, ldz, s));
   if (n_inc > 0) {
+    // copied from a pageable buffer of our own: cudaMemcpyAsync returns once the bytes are
+    // staged, so the call needs no synchronisation whatever memory the caller's `inc` is in
+    const std::vector<double> hinc(inc, inc + 9 * n_inc);
     Scratch dinc(s);
     FOSB_CUDA(dinc.alloc(sizeof(double) * 9 * n_inc));
-    FOSB_CUDA(cudaMemcpyAsync(dinc.p, inc, sizeof(double) * 9 * n_inc, cudaMemcpyHostToDevice, s));
+    FOSB_CUDA(cudaMemcpyAsync(dinc.p, hinc.data(), sizeof(double) * 9 * n_inc, cudaMemcpyHostToDevice, s));
     FOSB_CUDA(cudaMemset2DAsync(b, ldb * elem, 0, n_inc * elem, N, s));
     FOSB_CUDA(launch_rhs(mesh->d, k, dinc.as<double>(), n_inc, is_c64(prec), b, ldb, s));
-    FOSB_CUDA(cudaStreamSynchronize(s));  // the host incidence copy must finish before scratch reuse
   }
   return FOSB_OK;
 }
@@ -386,7 +388,9 @@ fosb_status fosb_factor(const void* Z, int64_t n, int64_t ldz, int prec, fosb_lu
     if (p < 0 || p >= n) return cleanup(fail(FOSB_ERR_CUDA, "fosb_factor: corrupt pivot"));
     std::swap(perm[i], perm[p]);
   }
-  if ((e = cudaMemcpy(lu->ipiv, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice)))
+  // stream-ordered (a plain cudaMemcpy would also wait for the legacy default stream's work);
+  // perm is pageable, so the call returns once it is staged
+  if ((e = cudaMemcpyAsync(lu->ipiv, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)))
     return cleanup(cuda_fail(e, "fosb_factor: permutation"));
   if (prec != FOSB_FP64) {  // inverted diagonal blocks for the streaming triangular sweeps
     if ((e = cudaMalloc(&lu->dinv, tri_block_inverses_bytes(n))) != cudaSuccess ||

@@ -6,6 +6,7 @@ covariance blocks, far-field moments).
 """
 from __future__ import annotations
 
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -72,6 +73,11 @@ class FOSBProblem:
     # relative trace error and forms each block as Y_l1 Y_l2^H (fosb_covariance_lowrank)
     lowrank_tol: float | None = None
     max_rank: int | None = None
+    # run the coarser levels' assembly, factorisation and solve on a high-priority side stream
+    # while the finest level's assembly runs, then the CT blocks without the finest level (in a
+    # host thread, on the same side stream) while it factors and solves: the levels and those
+    # blocks are independent of the finest level until the signed sum
+    overlap: bool = True
     levels: dict = field(default_factory=dict)
 
     def setup(self, device="cuda:0"):
@@ -91,21 +97,34 @@ class FOSBProblem:
     def nominal(self, l: int, timers=None):
         """A2-A6 for one level: assembly, factorisation, refined solve.  timers: optional
         dict name -> list of (start, end) CUDA events recorded on the current stream."""
+        self.assemble(l, timers)
+        self.factor_solve(l, timers)
+
+    @staticmethod
+    def _ev(timers, name, l):
         import torch
 
-        def ev(name):
-            if timers is None:
-                return None
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            timers.setdefault(f"{name}_l{l}", []).append((a, b))
-            a.record()
-            return b
+        if timers is None:
+            return None
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        timers.setdefault(f"{name}_l{l}", []).append((a, b))
+        a.record()
+        return b
 
+    def assemble(self, l: int, timers=None):
+        """A2-A4 for one level (enqueued on the current stream)."""
         st = self.levels[l]
-        e = ev("assemble")
+        e = self._ev(timers, "assemble", l)
         assemble_efie(st.mesh, self.k, st.Z, inc=self.inc, b=st.b, n_ss=self.n_ss, arith=self.arith, prec=self.prec)
         if e is not None:
             e.record()
+
+    def factor_solve(self, l: int, timers=None):
+        """A5-A6 for one level: factorisation and refined solve (both synchronise the stream)."""
+        import torch
+
+        st = self.levels[l]
+        ev = lambda name: self._ev(timers, name, l)
         e = ev("factor")
         st.lu = factor(st.Z, prec=self.prec)
         if e is not None:
@@ -128,20 +147,62 @@ class FOSBProblem:
         nd3 = 3 * self.dirs.shape[0]
         dt = self.levels[self.L].Z.dtype
         dev = self.levels[self.L].Z.device
-        for l in sorted(self.levels):
-            self.nominal(l, timers)
+        lv = sorted(self.levels)
+        fine = self.levels[self.L]
+        cov = torch.empty((nd3, nd3), dtype=dt, device=dev)
+        pcov = torch.empty((nd3, nd3), dtype=dt, device=dev) if self.pseudo else None
+        blocks = hermitian_blocks(self.L0, self.L)
+        early = []  # CT blocks computed beside the finest level's factorisation
+        if self.overlap and len(lv) > 1:
+            main = torch.cuda.current_stream()
+            if getattr(self, "_side", None) is None:
+                self._side = torch.cuda.Stream(device=dev, priority=-5)  # clamped to the highest priority
+            side = self._side
+            side.wait_stream(main)  # the coarse Z, b and the outputs may still be used by earlier work on main
+            self.assemble(lv[-1], timers)
+            with torch.cuda.stream(side):
+                for l in lv[:-1]:
+                    self.nominal(l, timers)
+            worker, err = None, []
+            if self.lowrank_tol is None:
+                # the blocks without the finest level need none of its results: a host thread
+                # computes them on the side stream while this one factors and solves level L
+                early = [b for b in blocks if self.L not in b[0]]
+
+                def coarse():
+                    try:
+                        torch.cuda.set_device(dev)
+                        with torch.cuda.stream(side):
+                            self._full_blocks(cov, pcov, early, first=True)
+                    except BaseException as e:  # re-raised by the caller after the join
+                        err.append(e)
+
+                if early:
+                    cov.record_stream(side)
+                    if pcov is not None:
+                        pcov.record_stream(side)
+                    worker = threading.Thread(target=coarse, name="fosb-ct-coarse-blocks")
+                    worker.start()
+            try:
+                self.factor_solve(lv[-1], timers)
+            finally:
+                if worker is not None:
+                    worker.join()
+            if err:
+                raise err[0]
+            main.wait_stream(side)
+        else:
+            for l in lv:
+                self.nominal(l, timers)
         if timers is not None:
             cov_start = torch.cuda.Event(enable_timing=True)
             cov_start.record()
-        fine = self.levels[self.L]
         F = torch.empty((nd3, 1), dtype=dt, device=dev)
         farfield_moments(fine.mesh, self.k, self.dirs, fine.u, F, prec=self.prec)
-        cov = torch.empty((nd3, nd3), dtype=dt, device=dev)
-        pcov = torch.empty((nd3, nd3), dtype=dt, device=dev) if self.pseudo else None
         if self.lowrank_tol is not None:
             self._lowrank_blocks(cov, pcov)
         else:
-            self._full_blocks(cov, pcov)
+            self._full_blocks(cov, pcov, [b for b in blocks if b not in early], first=not early)
         # A11: RCS_dB of the mean field and the variance of every far-field component; with the
         # pseudo-covariance also the delta-method variance of RCS_dB (device float64 tensors)
         n_dir = self.dirs.shape[0]
@@ -155,13 +216,13 @@ class FOSBProblem:
             timers.setdefault("covariance_ct", []).append((cov_start, cov_end))
         return (F, cov) if pcov is None else (F, cov, pcov)
 
-    def _full_blocks(self, cov, pcov):
-        """CT sum over the Hermitian blocks, each Sigma_{l1,l2} from fosb_covariance and
-        projected by fosb_farfield_moments (mirrored when l1 != l2)."""
+    def _full_blocks(self, cov, pcov, blocks, first=True):
+        """CT sum over `blocks` ((l1, l2), sign) of the Hermitian blocks, each Sigma_{l1,l2}
+        from fosb_covariance and projected by fosb_farfield_moments (mirrored when l1 != l2);
+        first: the first block overwrites the outputs, the others add to them."""
         import torch
 
-        first = True
-        for (l1, l2), sgn in hermitian_blocks(self.L0, self.L):
+        for (l1, l2), sgn in blocks:
             a, c = self.levels[l1], self.levels[l2]
             for pseudo, out in ((False, cov), (True, pcov)):
                 if out is None:

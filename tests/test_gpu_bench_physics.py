@@ -63,6 +63,26 @@ def test_sphere_ka4_ct_levels_0_to_3_match_oracle(F):
     prob.release()
 
 
+def test_level_overlap_gives_the_sequential_result(F):
+    """The coarse levels on a side stream beside the finest level's assembly (the default)
+    give the sequential step's result (only the order of the FP64 atomics may differ)."""
+    from paper_2308_01457_gb300.ct import FOSBProblem
+
+    k, sig, ell = 4.0, 0.005, 0.3
+    dirs = S.hplane_directions(31)
+    meshes = [S.icosphere(l + 1) for l in range(3)]
+    outs = []
+    for overlap in (True, False):
+        prob = FOSBProblem(meshes, k, (0, 0, 1), (1, 0, 0), dirs, 0, 2, F.COV_GAUSS, sig, ell, prec=F.MIXED,
+                           arith=F.ASM_FF, pseudo=True, overlap=overlap).setup()
+        for _ in range(2):  # the second step reuses the buffers of the first
+            res = [t.cpu().numpy() for t in prob.run()]
+            prob.release()
+        outs.append(res)
+    for a, b in zip(*outs):
+        assert _rel(a, b) < 1e-12
+
+
 def test_batched_level4_ellipsoids_match_oracle(F):
     table = S.batched_ellipsoid_table()
     picked = [(i, row) for i, row in enumerate(table) if row[2] == 4][:2]
