@@ -133,3 +133,21 @@ def test_lowrank_arguments_are_checked(F):
     with pytest.raises(F.FosbError) as ei:
         F.kernel_lowrank([m], F.COV_GAUSS, 1.0, 0.5, tol=-1.0, device=DEV)
     assert ei.value.status == F.FOSB_ERR_INVALID_ARG
+
+
+def test_lowrank_fp32_path_matches_oracle_at_fp32_accuracy(F):
+    """complex64 factors without refinement: the low-rank covariance (complex64 Y) agrees
+    with the oracle's full covariance at the FP32 path's 1e-4."""
+    from paper_2308_01457_gb300.ct import FOSBProblem
+
+    k, sig, ell = 1.5, 0.3, 0.6
+    dirs = S.hplane_directions(7)
+    meshes = [S.icosphere(l + 1) for l in range(2)]
+    prob = FOSBProblem(meshes, k, (0, 0, 1), (1, 0, 0), dirs, 0, 1, F.COV_GAUSS, sig, ell, prec=F.FP32,
+                       arith=F.ASM_FP32, lowrank_tol=1e-12).setup()
+    _, cov = prob.run()
+    assert cov.dtype == torch.complex64
+    lev = {l: O.nominal_level(O.from_synth(sm), k, [0, 0, 1], [1, 0, 0], dirs) for l, sm in enumerate(meshes)}
+    cov_o = O.ct_farfield_covariance(lev, 0, 1, "gauss", sig, ell)
+    assert _rel(cov.cpu().numpy().astype(np.complex128), cov_o) < 1e-4
+    prob.release()
