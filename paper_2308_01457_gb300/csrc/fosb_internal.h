@@ -231,6 +231,10 @@ size_t getrf_scratch_bytes(int64_t max_ctas, bool c128);
 size_t tslu_scratch_bytes(int64_t n_max);
 cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, int64_t row_base, void* scratch,
                        int64_t n_max, int* d_status, cudaStream_t s);
+// X (jb x ncols, leading dimension ldx) := L^{-1} X, L the unit lower jb x jb block at D
+// (leading dimension ldd), complex64, jb <= 64: a thread per column (tslu.cu).
+cudaError_t tri_lower_unit_cols(const void* D, int64_t ldd, int jb, void* X, int64_t ldx, int64_t ncols,
+                                cudaStream_t s);
 // The row interchanges of the last tslu_panel on the same scratch, applied to the columns
 // of the n-column matrix A outside the panel's columns [j0, j0 + jb) (rows from j0 on).
 cudaError_t tslu_swap(void* A, int64_t n, int64_t lda, int64_t j0, int jb, const void* scratch, cudaStream_t s);

@@ -1304,9 +1304,13 @@ fosb_status getrf(void* Av, int64_t n, int64_t lda, int32_t* ipiv, int* d_status
   };
   // X (jb rows x ncols, ld lda) := L^{-1} X with L the unit lower jb x jb block at D
   auto trsm_lower = [&](const V* D, int jb, V* X, int64_t ncols) -> cudaError_t {
-    enable_trsv_smem<T>();
-    trsv_warp_kernel<T><<<cdiv(ncols, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(D, lda, jb, 0, X, lda, ncols);
-    return launched();
+    if constexpr (sizeof(T) == 4) {
+      return tri_lower_unit_cols(D, lda, jb, X, lda, ncols, s);  // a thread per column
+    } else {
+      enable_trsv_smem<T>();
+      trsv_warp_kernel<T><<<cdiv(ncols, 8), 256, size_t(jb) * jb * sizeof(V), s>>>(D, lda, jb, 0, X, lda, ncols);
+      return launched();
+    }
   };
   if constexpr (sizeof(T) == 4) {
     // complex64 factors: outer blocks of NB = 256 columns, each factored as four 64-column

@@ -387,46 +387,122 @@ __global__ void __launch_bounds__(256) tslu_apply_kernel(float2* __restrict__ A,
   }
 }
 
-// L21 = A21 U11^{-1} for rows [jb, m): one warp per row, lanes own columns (lane, lane + 32).
-__global__ void __launch_bounds__(256) tslu_lsolve_kernel(float2* __restrict__ A, int64_t lda, int64_t m, int jb) {
-  __shared__ float2 s_U[kTsluCols][kTsluCols];
-  __shared__ float2 s_dinv[kTsluCols];
-  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x) {
-    const int r = e / jb, c = e % jb;
-    s_U[r][c] = A[int64_t(r) * lda + c];
+// Triangular substitution on per-thread vectors of 64 complex values held transposed in
+// shared memory (element k of this thread's vector at xs[k * ldx]): for k = 0 .. 63,
+// x_k *= dinv_k (kScale) and x_c -= x_k M[k][c] for c > k, the right-looking order of
+// forward substitution.  The vector is taken 8 elements at a time: the 8 live in registers
+// while the chunk is solved, then one rank-8 update reaches every later element (the same
+// operations in the same order as one element at a time).  M is in shared memory and read
+// by every thread alike (broadcast).
+template <bool kScale>
+__device__ __forceinline__ void tri_chunked(float2* xs, int ldx, const float2 (*M)[kTsluCols], const float2* dinv) {
+#pragma unroll 1
+  for (int k0 = 0; k0 < kTsluCols; k0 += 8) {
+    float2 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = xs[(k0 + i) * ldx];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (kScale) x[i] = cmulf(x[i], dinv[k0 + i]);
+#pragma unroll
+      for (int q = i + 1; q < 8; ++q) cfms(x[q], x[i], M[k0 + i][k0 + q]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xs[(k0 + i) * ldx] = x[i];
+#pragma unroll 4
+    for (int c = k0 + 8; c < kTsluCols; ++c) {
+      float2 y = xs[c * ldx];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cfms(y, x[i], M[k0 + i][c]);
+      xs[c * ldx] = y;
+    }
+  }
+}
+
+constexpr int kLsRows = 64;  // rows (threads) per CTA of the L21 solve
+constexpr int kLsLd = kLsRows + 1;
+constexpr size_t kLsSmem = size_t(kTsluCols) * kTsluCols * sizeof(float2) + kTsluCols * sizeof(float2) +
+                           size_t(kTsluCols) * kLsLd * sizeof(float2);
+
+// L21 = A21 U11^{-1} for rows [jb, m), U11 the upper triangle (with the diagonal) of the top
+// jb rows: a thread per row.  The CTA's 64 rows are loaded with coalesced row reads, 8 rows
+// in flight per warp, into a transposed shared tile; U11 is staged identity-padded to
+// 64 x 64, so a ragged panel (jb < 64) needs no other case.
+__global__ void __launch_bounds__(kLsRows) tslu_lsolve_kernel(float2* __restrict__ A, int64_t lda, int64_t m, int jb) {
+  extern __shared__ float4 ls_raw[];
+  auto sM = reinterpret_cast<float2 (*)[kTsluCols]>(ls_raw);
+  float2* s_dinv = reinterpret_cast<float2*>(ls_raw) + kTsluCols * kTsluCols;
+  float2* xs = s_dinv + kTsluCols;  // [64][kLsLd]
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int kWarps = kLsRows / 32, kBatch = 8;
+  for (int e = t; e < kTsluCols * kTsluCols; e += kLsRows) {
+    const int r = e / kTsluCols, c = e % kTsluCols;
+    sM[r][c] = (r < jb && c < jb && c >= r) ? A[int64_t(r) * lda + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  if (threadIdx.x < jb) s_dinv[threadIdx.x] = cinv(s_U[threadIdx.x][threadIdx.x]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  // grid-stride over rows, so U11 is staged once per CTA
-  for (int64_t row = jb + int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5); row < m; row += int64_t(gridDim.x) * 8) {
-    float2* x = A + row * lda;
-    float2 x0 = lane < jb ? x[lane] : make_float2(0.f, 0.f);
-    float2 x1 = lane + 32 < jb ? x[lane + 32] : make_float2(0.f, 0.f);
-    for (int k = 0; k < jb; ++k) {
-      // l_k = (a_k - sum_{i<k} l_i u_ik) / u_kk: the owner lane finishes it, then all
-      // later columns subtract l_k u_kc
-      float2 v = k < 32 ? x0 : x1;
-      v.x = __shfl_sync(0xffffffffu, v.x, k & 31);
-      v.y = __shfl_sync(0xffffffffu, v.y, k & 31);
-      const float2 l = cmulf(v, s_dinv[k]);
-      if (k < 32 && lane == k) x0 = l;
-      if (k >= 32 && lane == k - 32) x1 = l;
-      if (lane > k && lane < jb) {
-        const float2 u = s_U[k][lane];
-        x0.x -= l.x * u.x - l.y * u.y;
-        x0.y -= l.x * u.y + l.y * u.x;
-      }
-      if (lane + 32 > k && lane + 32 < jb) {
-        const float2 u = s_U[k][lane + 32];
-        x1.x -= l.x * u.x - l.y * u.y;
-        x1.y -= l.x * u.y + l.y * u.x;
+  s_dinv[t] = t < jb ? cinv(sM[t][t]) : make_float2(1.f, 0.f);
+  const int64_t r0 = jb + int64_t(blockIdx.x) * kLsRows;
+  for (int b0 = warp; b0 < kLsRows; b0 += kWarps * kBatch) {
+    float2 v[kBatch][2];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int rr = b0 + b * kWarps;
+      const int64_t row = r0 + rr;
+      const bool ok = rr < kLsRows && row < m;
+      v[b][0] = (ok && lane < jb) ? A[row * lda + lane] : make_float2(0.f, 0.f);
+      v[b][1] = (ok && lane + 32 < jb) ? A[row * lda + lane + 32] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int rr = b0 + b * kWarps;
+      if (rr < kLsRows) {
+        xs[lane * kLsLd + rr] = v[b][0];
+        xs[(lane + 32) * kLsLd + rr] = v[b][1];
       }
     }
-    if (lane < jb) x[lane] = x0;
-    if (lane + 32 < jb) x[lane + 32] = x1;
   }
+  __syncthreads();
+  tri_chunked<true>(xs + t, kLsLd, sM, s_dinv);
+  __syncthreads();
+  for (int rr = warp; rr < kLsRows; rr += kWarps) {
+    const int64_t row = r0 + rr;
+    if (row >= m) break;
+    if (lane < jb) A[row * lda + lane] = xs[lane * kLsLd + rr];
+    if (lane + 32 < jb) A[row * lda + lane + 32] = xs[(lane + 32) * kLsLd + rr];
+  }
+}
+
+constexpr int kLcCols = 64;  // columns (threads) per CTA of the unit-lower column solve
+constexpr int kLcLd = kLcCols + 1;
+constexpr size_t kLcSmem = size_t(kTsluCols) * kTsluCols * sizeof(float2) + size_t(kTsluCols) * kLcLd * sizeof(float2);
+
+// X (jb x ncols, leading dimension ldx) := L^{-1} X with L the unit lower jb x jb block at
+// D (leading dimension ldd): a thread per column, M[k][c] = L[c][k] staged zero-padded.
+__global__ void __launch_bounds__(kLcCols) tri_lower_unit_cols_kernel(const float2* __restrict__ D, int64_t ldd, int jb,
+                                                                      float2* __restrict__ X, int64_t ldx,
+                                                                      int64_t ncols) {
+  extern __shared__ float4 lc_raw[];
+  auto sM = reinterpret_cast<float2 (*)[kTsluCols]>(lc_raw);
+  float2* xs = reinterpret_cast<float2*>(lc_raw) + kTsluCols * kTsluCols;  // [64][kLcLd]
+  const int t = threadIdx.x;
+  for (int e = t; e < kTsluCols * kTsluCols; e += kLcCols) {
+    const int k = e / kTsluCols, c = e % kTsluCols;
+    sM[k][c] = (k < jb && c < jb && c > k) ? D[int64_t(c) * ldd + k] : make_float2(0.f, 0.f);
+  }
+  const int64_t col = int64_t(blockIdx.x) * kLcCols + t;
+  const bool ok = col < ncols;
+  constexpr int kBatch = 16;
+  for (int k0 = 0; k0 < kTsluCols; k0 += kBatch) {
+    float2 v[kBatch];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) v[b] = (ok && k0 + b < jb) ? X[int64_t(k0 + b) * ldx + col] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) xs[(k0 + b) * kLcLd + t] = v[b];
+  }
+  __syncthreads();
+  tri_chunked<false>(xs + t, kLcLd, sM, nullptr);
+  if (!ok) return;
+  for (int k = 0; k < jb; ++k) X[int64_t(k) * ldx + col] = xs[k * kLcLd + t];
 }
 
 // The panel's row permutation on the columns outside it (left: earlier L columns; right:
@@ -508,13 +584,36 @@ cudaError_t tslu_panel(void* Ap, int64_t m, int jb, int64_t lda, int32_t* ipiv, 
   tslu_apply_kernel<<<1, 256, 0, s>>>(A, lda, jb, sel, top, ipiv, row_base, d_status, moves);
   ++nl;
   if (m > jb) {
-    static int nsm[64] = {};
-    if (!nsm[dev]) cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
-    const unsigned g = std::min<unsigned>(cdivu(m - jb, 8), unsigned(6 * std::max(nsm[dev], 1)));
-    tslu_lsolve_kernel<<<g, 256, 0, s>>>(A, lda, m, jb);
+    static bool ls_attr[64] = {};
+    if (!ls_attr[dev]) {
+      const cudaError_t e = cudaFuncSetAttribute(tslu_lsolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(kLsSmem));
+      if (e != cudaSuccess) return e;
+      ls_attr[dev] = true;
+    }
+    tslu_lsolve_kernel<<<cdivu(m - jb, kLsRows), kLsRows, kLsSmem, s>>>(A, lda, m, jb);
     ++nl;
   }
   return launched(nl);
+}
+
+cudaError_t tri_lower_unit_cols(const void* D, int64_t ldd, int jb, void* X, int64_t ldx, int64_t ncols,
+                                cudaStream_t s) {
+  if (jb <= 0 || jb > kTsluCols) return cudaErrorInvalidValue;
+  if (ncols <= 0) return cudaSuccess;
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(tri_lower_unit_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLcSmem));
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  tri_lower_unit_cols_kernel<<<cdivu(ncols, kLcCols), kLcCols, kLcSmem, s>>>(static_cast<const float2*>(D), ldd, jb,
+                                                                            static_cast<float2*>(X), ldx, ncols);
+  return launched();
 }
 
 cudaError_t tslu_swap(void* A, int64_t n, int64_t lda, int64_t j0, int jb, const void* scratch, cudaStream_t s) {

@@ -55,7 +55,7 @@ def test_gmres_ir_converges_where_refinement_stalls(F):
     # an independent complex128 backward error, and LAPACK's solution to kappa * eps
     r = b - A @ xh
     be = np.abs(r).max(axis=0) / (np.abs(A).sum(axis=1).max() * np.abs(xh).max(axis=0) + np.abs(b).max(axis=0))
-    assert be.max() < 1e-14, be
+    assert be.max() <= 2.0 * tol, be  # the stopping rule's bound (x2 for a different summation order)
     xl = np.linalg.solve(A, b)
     assert np.linalg.norm(xh - xl) / np.linalg.norm(xl) < 100 * kappa * 2.0**-52
 
