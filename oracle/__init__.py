@@ -218,6 +218,82 @@ def rcs_db(F: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Dielectric scatterer: the PMCHWT system (Section II-C eq. pmchwt)
+# ---------------------------------------------------------------------------
+def dielectric_wavenumbers(k0: float, eps_r: float, mu_r: float):
+    """k1 = k0 sqrt(eps_r mu_r) inside and eta = sqrt(mu_r/eps_r) (Section II-A,
+    eq. relativeParameters; k_i = omega sqrt(mu_i eps_i))."""
+    return k0 * math.sqrt(eps_r * mu_r), math.sqrt(mu_r / eps_r)
+
+
+def assemble_mfio(mesh: RWGMesh, k: float, n_ss: int = 5, threads: int | None = None) -> np.ndarray:
+    """<K_k f_n, f_m>_x (N x N): the MFIO K_k = {gamma_D H_k} of Section II-B tested with
+    the x-pairing, -int int (x - y).(f_n(y) x f_m(x)) exp(ikr)(ikr - 1)/(4 pi r^3)."""
+    qb, qw = triangle_rule6()
+    gx, gw = gauss_legendre01(n_ss)
+    N = mesh.n_edges
+    K = np.zeros((N, N), dtype=np.complex128)
+    _load().orc_assemble_mfio(*mesh._args(), ctypes.c_int64(N), ctypes.c_double(k), _p(qb), _p(qw), ctypes.c_int(6),
+                              _p(gx), _p(gw), ctypes.c_int(n_ss), _p(K), ctypes.c_int(threads or n_threads()))
+    return K
+
+
+def mfio_block(mesh: RWGMesh, k: float, t1: int, t2: int, n_ss: int = 5) -> np.ndarray:
+    """3 x 3 MFIO block of the triangle pair (t1 test, t2 trial), local edges in order."""
+    qb, qw = triangle_rule6()
+    gx, gw = gauss_legendre01(n_ss)
+    out = np.zeros((3, 3), dtype=np.complex128)
+    _load().orc_mfio_block(*mesh._args(), ctypes.c_double(k), _p(qb), _p(qw), ctypes.c_int(6), _p(gx), _p(gw),
+                           ctypes.c_int(n_ss), ctypes.c_int64(t1), ctypes.c_int64(t2), _p(out))
+    return out
+
+
+def assemble_pmchwt(mesh: RWGMesh, k0: float, eps_r: float, mu_r: float, n_ss: int = 5,
+                    threads: int | None = None) -> np.ndarray:
+    """Galerkin matrix (2N x 2N) of A_0 + A^_1 (Section II-C eq. pmchwt; A_k and the scaled
+    A^_k of eq. BOmultitraceA) for the exterior Cauchy data (j, m) = (gamma_D^c E, gamma_N^c E):
+      [[K_0 + K_1, T_0 + eta T_1], [-T_0 - T_1/eta, K_0 + K_1]]."""
+    k1, eta = dielectric_wavenumbers(k0, eps_r, mu_r)
+    qb, qw = triangle_rule6()
+    gx, gw = gauss_legendre01(n_ss)
+    N = mesh.n_edges
+    Z = np.zeros((2 * N, 2 * N), dtype=np.complex128)
+    _load().orc_assemble_pmchwt(*mesh._args(), ctypes.c_int64(N), ctypes.c_double(k0), ctypes.c_double(k1),
+                                ctypes.c_double(eta), _p(qb), _p(qw), ctypes.c_int(6), _p(gx), _p(gw),
+                                ctypes.c_int(n_ss), _p(Z), ctypes.c_int(threads or n_threads()))
+    return Z
+
+
+def rhs_pmchwt(mesh: RWGMesh, k0: float, d, p) -> np.ndarray:
+    """Tested incident Cauchy data (2N x n_inc): <gamma_D E_inc, f_m>_x = -int E_inc . f_m on
+    top and <gamma_N E_inc, f_m>_x = -int (curl E_inc/(ik0)) . f_m below; for
+    E_inc = p exp(ik0 d.x), curl E_inc/(ik0) = (d x p) exp(ik0 d.x) (Section V eq. incidentNumexp)."""
+    d = np.atleast_2d(np.asarray(d, dtype=np.float64))
+    p = np.atleast_2d(np.asarray(p, dtype=np.complex128))
+    return np.vstack([rhs_planewave(mesh, k0, d, p), rhs_planewave(mesh, k0, d, np.cross(d, p))])
+
+
+def farfield_matrix_pmchwt(mesh: RWGMesh, k0: float, xhat) -> np.ndarray:
+    """A (3 n_dir x 2N): F(xh) = -ik0 [xh x sum j_n v_n + (I - xh xh^T) sum m_n v_n],
+    v_n = int f_n exp(-ik0 xh.y), from E_sc = -E_k0 m - H_k0 j outside (Section II-C)."""
+    xhat = np.ascontiguousarray(np.atleast_2d(xhat), dtype=np.float64)
+    qb, qw = triangle_rule6()
+    A = np.zeros((3 * xhat.shape[0], 2 * mesh.n_edges), dtype=np.complex128)
+    _load().orc_farfield_matrix_pmchwt(*mesh._args(), ctypes.c_int64(mesh.n_edges), ctypes.c_double(k0), _p(qb),
+                                       _p(qw), ctypes.c_int(6), _p(xhat), ctypes.c_int64(xhat.shape[0]), _p(A))
+    return A
+
+
+def dielectric_farfield(mesh: RWGMesh, k0: float, eps_r: float, mu_r: float, d, p, xhat, n_ss: int = 5):
+    """Assemble, solve (LAPACK) and map the PMCHWT problem: returns (Z, b, x, F (n_dir x 3))."""
+    Z = assemble_pmchwt(mesh, k0, eps_r, mu_r, n_ss)
+    b = rhs_pmchwt(mesh, k0, d, p)
+    x = solve(Z, b)
+    F = (farfield_matrix_pmchwt(mesh, k0, xhat) @ x[:, 0]).reshape(-1, 3)
+    return Z, b, x, F
+
+
+# ---------------------------------------------------------------------------
 # Shape derivative, covariance, combination technique (Sections III and IV)
 # ---------------------------------------------------------------------------
 def triangle_normals(mesh: RWGMesh) -> np.ndarray:

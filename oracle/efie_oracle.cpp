@@ -18,6 +18,9 @@
 //   * the shape-derivative right-hand side of Section III, PEC case, in weak form:
 //       g_m = - sum_n u_n int v_n [ ik f_m.f_n + 1/(ik) div f_m div f_n ],
 //     v_n = sum_p xi_p psi_p nu_{p,T} (P1 hat psi_p, nu_{p,T} = n_p . n_T).
+//   * the dielectric (PMCHWT) system of Section II-C: the MFIO blocks
+//     <K_k f_n, f_m>_x, K_k = {gamma_D H_k}, the 2N x 2N matrix of A_0 + A^_1 and the
+//     far field of the exterior Cauchy data (j, m).
 //
 // RWG functions (lowest-order div-conforming, Section IV): on the triangle T with
 // opposite vertex p, f = s l/(2 A_T) (x - p), div f = s l/A_T, s = +1 on the
@@ -250,6 +253,59 @@ void pair_block(const MeshView& m, const Rules& q, double k, int64_t t1, int64_t
     for (int j = 0; j < 3; ++j) blk[i][j] = tb[j][i];
 }
 
+// ---- MFIO blocks for the dielectric (PMCHWT) system of Section II-C -----------------
+// K_k = {gamma_D H_k}, H_k v = curl int G v (Section II-B).  Tested with the x-pairing:
+//   <K_k f_n, f_m>_x = -int f_m(x) . (curl_x int G(x,y) f_n(y) dy) dx
+//                    = -int int (x - y) . (f_n(y) x f_m(x)) G'(r)/r,
+//   G'(r)/r = exp(ikr) (ikr - 1) / (4 pi r^3),  r = |x - y|,
+// the principal value: on one flat triangle x - y lies in the plane and f_n x f_m is
+// normal to it, so identical pairs contribute nothing and need no special rule.
+void add_point_pair_mfio(double k, const LocalRWG& f, const LocalRWG& g, Vec3 x, Vec3 y, double w, cplx blk[3][3]) {
+  Vec3 d = sub(x, y);
+  double r = norm(d);
+  cplx gk = std::exp(cplx(0.0, k * r)) * cplx(-1.0, k * r) / (4.0 * M_PI * r * r * r) * w;
+  for (int i = 0; i < 3; ++i) {
+    Vec3 fi = scale(sub(x, f.opp[i]), f.coef[i]);
+    for (int j = 0; j < 3; ++j) {
+      Vec3 gj = scale(sub(y, g.opp[j]), g.coef[j]);
+      blk[i][j] += -gk * dot(d, cross(gj, fi));
+    }
+  }
+}
+
+// 3 x 3 MFIO block of the ordered triangle pair (t1 test, t2 trial), with the same rules
+// as the EFIO blocks (6-point rule in x and y for vertex-disjoint pairs, Sauter-Schwab
+// with t1 < t2 and the transpose for touching ones; the block is symmetric under
+// exchanging the two triangles, as the EFIO's is).
+void pair_block_mfio(const MeshView& m, const Rules& q, double k, int64_t t1, int64_t t2, cplx blk[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) blk[i][j] = 0.0;
+  Vec3 P[3], Q[3];
+  PairKind kind = classify(m, t1, t2, P, Q);
+  if (kind == REGULAR) {
+    LocalRWG f = local_rwg(m, t1), g = local_rwg(m, t2);
+    double A1 = m.area(t1), A2 = m.area(t2);
+    Vec3 a0 = m.tv(t1, 0), a1 = m.tv(t1, 1), a2 = m.tv(t1, 2);
+    Vec3 b0 = m.tv(t2, 0), b1 = m.tv(t2, 1), b2 = m.tv(t2, 2);
+    for (int p = 0; p < q.nq; ++p) {
+      Vec3 x = add(add(scale(a0, q.qb[3 * p]), scale(a1, q.qb[3 * p + 1])), scale(a2, q.qb[3 * p + 2]));
+      for (int s = 0; s < q.nq; ++s) {
+        Vec3 y = add(add(scale(b0, q.qb[3 * s]), scale(b1, q.qb[3 * s + 1])), scale(b2, q.qb[3 * s + 2]));
+        add_point_pair_mfio(k, f, g, x, y, q.qw[p] * A1 * q.qw[s] * A2, blk);
+      }
+    }
+    return;
+  }
+  int64_t a = t1 < t2 ? t1 : t2, b = t1 < t2 ? t2 : t1;
+  if (t1 > t2) classify(m, a, b, P, Q);
+  LocalRWG f = local_rwg(m, a), g = local_rwg(m, b);
+  double jac = (2.0 * m.area(a)) * (2.0 * m.area(b));
+  cplx tb[3][3] = {};
+  ss_points(kind, P, Q, q, jac, [&](Vec3 x, Vec3 y, double w) { add_point_pair_mfio(k, f, g, x, y, w, tb); });
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) blk[i][j] = t1 <= t2 ? tb[i][j] : tb[j][i];
+}
+
 }  // namespace
 
 extern "C" {
@@ -432,6 +488,147 @@ int orc_sd_rhs(const double* verts, const int32_t* tris, int64_t nt, const int32
         vals[2 * (9 * t + 3 * i + a)] = acc[i][a].real();
         vals[2 * (9 * t + 3 * i + a) + 1] = acc[i][a].imag();
       }
+  }
+  return 0;
+}
+
+// Galerkin matrix of the PMCHWT operator A_0 + A^_1 (Section II-C eq. pmchwt, with the
+// multitrace operators of eq. BOmultitraceA) for the exterior Cauchy data (j, m):
+//   Z (2N x 2N) = [[ K_0 + K_1,        T_0 + eta T_1 ],
+//                  [ -T_0 - T_1 / eta,  K_0 + K_1     ]],
+// T_k the EFIO blocks above, K_k the MFIO blocks, k = k0 outside and k1 inside.
+int orc_assemble_pmchwt(const double* verts, const int32_t* tris, int64_t nt, const int32_t* tri_edge,
+                        const double* tri_sign, const double* edge_len, int64_t n_edges, double k0, double k1,
+                        double eta, const double* qb, const double* qw, int nq, const double* glx, const double* glw,
+                        int nss, double* Z, int nthreads) {
+  MeshView m{verts, tris, nt, tri_edge, tri_sign, edge_len};
+  Rules q{qb, qw, nq, glx, glw, nss};
+  const int64_t N = n_edges, ld = 2 * n_edges;
+  std::memset(Z, 0, sizeof(double) * 2 * ld * ld);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t t1 = 0; t1 < nt; ++t1) {
+    for (int64_t t2 = 0; t2 < nt; ++t2) {
+      cplx T0[3][3], T1[3][3], K0[3][3], K1[3][3];
+      pair_block(m, q, k0, t1, t2, T0);
+      pair_block(m, q, k1, t1, t2, T1);
+      pair_block_mfio(m, q, k0, t1, t2, K0);
+      pair_block_mfio(m, q, k1, t1, t2, K1);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          const int64_t r = tri_edge[3 * t1 + i], c = tri_edge[3 * t2 + j];
+          const cplx kk = K0[i][j] + K1[i][j];
+          const cplx v[4] = {kk, T0[i][j] + eta * T1[i][j], -T0[i][j] - T1[i][j] / eta, kk};
+          const int64_t idx[4] = {r * ld + c, r * ld + N + c, (N + r) * ld + c, (N + r) * ld + N + c};
+          for (int e = 0; e < 4; ++e) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            Z[2 * idx[e]] += v[e].real();
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            Z[2 * idx[e] + 1] += v[e].imag();
+          }
+        }
+    }
+  }
+  return 0;
+}
+
+// MFIO matrix alone, <K_k f_n, f_m>_x (N x N), for the oracle's own pins.
+int orc_assemble_mfio(const double* verts, const int32_t* tris, int64_t nt, const int32_t* tri_edge,
+                      const double* tri_sign, const double* edge_len, int64_t n_edges, double k, const double* qb,
+                      const double* qw, int nq, const double* glx, const double* glw, int nss, double* K,
+                      int nthreads) {
+  MeshView m{verts, tris, nt, tri_edge, tri_sign, edge_len};
+  Rules q{qb, qw, nq, glx, glw, nss};
+  std::memset(K, 0, sizeof(double) * 2 * n_edges * n_edges);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t t1 = 0; t1 < nt; ++t1) {
+    for (int64_t t2 = 0; t2 < nt; ++t2) {
+      cplx blk[3][3];
+      pair_block_mfio(m, q, k, t1, t2, blk);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          int64_t idx = 2 * (int64_t(tri_edge[3 * t1 + i]) * n_edges + tri_edge[3 * t2 + j]);
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+          K[idx] += blk[i][j].real();
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+          K[idx + 1] += blk[i][j].imag();
+        }
+    }
+  }
+  return 0;
+}
+
+// One 3 x 3 MFIO block (t1 test, t2 trial) for the oracle's pins.
+int orc_mfio_block(const double* verts, const int32_t* tris, int64_t nt, const int32_t* tri_edge,
+                   const double* tri_sign, const double* edge_len, double k, const double* qb, const double* qw, int nq,
+                   const double* glx, const double* glw, int nss, int64_t t1, int64_t t2, double* out) {
+  MeshView m{verts, tris, nt, tri_edge, tri_sign, edge_len};
+  Rules q{qb, qw, nq, glx, glw, nss};
+  cplx blk[3][3];
+  pair_block_mfio(m, q, k, t1, t2, blk);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      out[2 * (3 * i + j)] = blk[i][j].real();
+      out[2 * (3 * i + j) + 1] = blk[i][j].imag();
+    }
+  return 0;
+}
+
+// Far-field matrix of the dielectric problem (3 n_dir x 2N) for the exterior Cauchy data
+// (j, m): the scattered field outside is E_sc = -E_k m - H_k j (Section II-C, the
+// representation E = E_inc + R(xi) with R = (-H, -E)), so with v_n = int f_n(y) exp(-ik xh.y) dy
+//   F(xh) = -ik [ xh x sum_n j_n v_n + (I - xh xh^T) sum_n m_n v_n ].
+int orc_farfield_matrix_pmchwt(const double* verts, const int32_t* tris, int64_t nt, const int32_t* tri_edge,
+                               const double* tri_sign, const double* edge_len, int64_t n_edges, double k,
+                               const double* qb, const double* qw, int nq, const double* xh, int64_t n_dir,
+                               double* Aout) {
+  MeshView m{verts, tris, nt, tri_edge, tri_sign, edge_len};
+  const int64_t ld = 2 * n_edges;
+  std::memset(Aout, 0, sizeof(double) * 2 * 3 * n_dir * ld);
+  const cplx ik(0.0, k);
+  for (int64_t t = 0; t < nt; ++t) {
+    LocalRWG f = local_rwg(m, t);
+    double A = m.area(t);
+    Vec3 a0 = m.tv(t, 0), a1 = m.tv(t, 1), a2 = m.tv(t, 2);
+    for (int64_t dd = 0; dd < n_dir; ++dd) {
+      Vec3 u{xh[3 * dd], xh[3 * dd + 1], xh[3 * dd + 2]};
+      for (int i = 0; i < 3; ++i) {
+        cplx J[3] = {0.0, 0.0, 0.0};
+        for (int qp = 0; qp < nq; ++qp) {
+          Vec3 y = add(add(scale(a0, qb[3 * qp]), scale(a1, qb[3 * qp + 1])), scale(a2, qb[3 * qp + 2]));
+          cplx ph = std::exp(cplx(0.0, -k * dot(u, y))) * (qw[qp] * A);
+          Vec3 fi = scale(sub(y, f.opp[i]), f.coef[i]);
+          J[0] += fi.x * ph;
+          J[1] += fi.y * ph;
+          J[2] += fi.z * ph;
+        }
+        cplx uJ = u.x * J[0] + u.y * J[1] + u.z * J[2];
+        cplx Tm[3] = {J[0] - u.x * uJ, J[1] - u.y * uJ, J[2] - u.z * uJ};
+        cplx Xj[3] = {u.y * J[2] - u.z * J[1], u.z * J[0] - u.x * J[2], u.x * J[1] - u.y * J[0]};
+        int64_t n = tri_edge[3 * t + i];
+        for (int c = 0; c < 3; ++c) {
+          cplx vj = -ik * Xj[c], vm = -ik * Tm[c];
+          int64_t row = (3 * dd + c) * ld;
+          Aout[2 * (row + n)] += vj.real();
+          Aout[2 * (row + n) + 1] += vj.imag();
+          Aout[2 * (row + n_edges + n)] += vm.real();
+          Aout[2 * (row + n_edges + n) + 1] += vm.imag();
+        }
+      }
+    }
   }
   return 0;
 }
