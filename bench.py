@@ -59,6 +59,15 @@ WORKLOADS = {
     "lowrank-sphere-ka4-full-L3": dict(kind="lowrank", mesh="sphere", levels=[3], k=4.0, sigma=0.005, ell=0.3,
                                        n_dir=181, L0=3, L=3, d=(0, 0, 1), p=(1, 0, 0), dirs="hplane",
                                        kernel="gauss", tol=1e-10),
+    # dielectric sphere by the PMCHWT system (Section II-C; Section V-A, Table I: k0 = 3,
+    # eps_r = 2.1, mu_r = 1, d = x, p = z, 1801 angles in the z = 0 plane): the icosphere of
+    # 5120 triangles, 2N = 15360 unknowns; assembly of both wavenumbers, complex64 LU with
+    # FP64-class refinement, far field of the exterior Cauchy data
+    "pmchwt-sphere-k3-N15360": dict(kind="pmchwt", level=4, k=3.0, eps_r=2.1, mu_r=1.0, n_dir=1801,
+                                    d=(1, 0, 0), p=(0, 0, 1), oracle_level=3),
+    # the same kernels one level down (1280 triangles, 2N = 3840; Z 236 MB > L2): profiling captures
+    "pmchwt-sphere-k3-N3840": dict(kind="pmchwt", level=3, k=3.0, eps_r=2.1, mu_r=1.0, n_dir=1801,
+                                   d=(1, 0, 0), p=(0, 0, 1), oracle_level=2),
 }
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio of the part
@@ -663,6 +672,203 @@ def run_lowrank(args):
     print(json.dumps(line), flush=True)
 
 
+# algorithmic FP64 operations per point pair and wavenumber of the PMCHWT regular pairs: the
+# EFIO's 27 (distance 8, phase 1, G 2, 8 real-weighted complex moments 16) and the MFIO's 24
+# (its kernel exp(ikr)(ikr - 1)/r^3 from G: 10; its scalar and y-weighted moments: 14)
+PMCHWT_OPS_PER_POINT_PAIR = 51.0
+
+
+def run_pmchwt(args):
+    """The dielectric workload: one step = fosb_assemble_pmchwt (both wavenumbers and the
+    tested incident data), the complex64 LU of the 2N x 2N system (fosb_factor, MIXED), the
+    refined solve and the far field at 1801 angles (fosb_farfield_pmchwt)."""
+    import ctypes
+
+    import torch
+
+    import fosb_synth as S
+    import paper_2308_01457_gb300 as F
+
+    F.build.build()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    dev = f"cuda:{local}"
+    sm = S.icosphere(W["level"])
+    dirs = S.zplane_directions(W["n_dir"])
+    inc = F.incidence([W["d"]], [W["p"]])
+    upeaks = {kd: round(F.peak_microbench(kd), 2) for kd in ("fp32", "fp64", "tf32", "bf16")}
+    mesh = F.mesh_create(sm.verts, sm.tris, sm.vnormals)
+    N = mesh.n_edges
+    C128 = torch.complex128
+    Z = torch.empty((2 * N, 2 * N), dtype=C128, device=dev)
+    b = torch.empty((2 * N, 1), dtype=C128, device=dev)
+    out = torch.empty((3 * W["n_dir"], 1), dtype=C128, device=dev)
+
+    def step(m, prec, timers=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if timers is not None else None
+        if ev:
+            ev[0].record()
+        F.assemble_pmchwt(m, W["k"], W["eps_r"], W["mu_r"], Z, inc=inc, b=b)
+        if ev:
+            ev[1].record()
+        lu = F.factor(Z, prec=prec)
+        if ev:
+            ev[2].record()
+        X, _, berr = F.solve(lu, b)
+        if ev:
+            ev[3].record()
+        F.farfield_pmchwt(m, W["k"], dirs, X, out)
+        if ev:
+            ev[4].record()
+            torch.cuda.synchronize()
+            for i, name in enumerate(("assemble", "factor", "solve", "farfield")):
+                timers.setdefault(name, []).append(ev[i].elapsed_time(ev[i + 1]))
+        del lu
+        return berr
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step(mesh, F.MIXED)
+    barrier()
+    launches0 = F.lib().fosb_kernel_launches()
+    clocks = _clock_sampler(local) if rank == 0 else None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record()
+    for i in range(args.steps):
+        berr = step(mesh, F.MIXED)
+        ev[i + 1].record()
+    barrier()
+    clk = _clock_summary(clocks)
+    launches = int(F.lib().fosb_kernel_launches() - launches0)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, ws, "cuda")
+    F_mixed = out.cpu().numpy()[:, 0].copy()
+    # profiled pass after the timed region: phases and kernel families
+    families = ["pmchwt_regular", "pmchwt_singular", "lu_update", "lu_update64", "lu_panel", "gemm_ff", "gemm_oz",
+                "trsm_update", "oz_prep", "getrs"]
+    for fam in families:
+        F.lib().fosb_profile_read(fam.encode(), None, None, None)
+    timers = {}
+    F.lib().fosb_profile_enable(1)
+    for _ in range(2):
+        step(mesh, F.MIXED, timers)
+    torch.cuda.synchronize()
+    F.lib().fosb_profile_enable(0)
+    fam_stats = {}
+    for fam in families:
+        ms_c, n_c, w_c = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        F.lib().fosb_profile_read(fam.encode(), ctypes.byref(ms_c), ctypes.byref(n_c), ctypes.byref(w_c))
+        fam_stats[fam] = {"ms_per_step": ms_c.value / 2, "launches_per_step": n_c.value / 2,
+                          "work_per_step": w_c.value / 2}
+    phase = {k: round(statistics.mean(v), 2) for k, v in timers.items()}
+    peaks = _peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    tf32_peak = bf16 * TF32_PER_BF16
+    model = {
+        "pmchwt_regular": ("alu", PMCHWT_OPS_PER_POINT_PAIR, upeaks["fp64"], "pmchwt_regular_kernel (FP64)",
+                           f"{PMCHWT_OPS_PER_POINT_PAIR:.0f} algorithmic FP64 ops per point pair and wavenumber "
+                           "(work = point pairs of both launches); peak = the FP64 FMA pipe measured by "
+                           "fosb_peak_microbench"),
+        "lu_update": ("tensor", 1.0, tf32_peak, "cgemm_update_split_kernel (tcgen05 kind::tf32, 3xTF32 complex)",
+                      "TF32 dense = measured bf16 sustained x 1.1/2.25; work = useful complex flops 8MNK"),
+        "lu_panel": ("latency", 1.0, None, "tslu_gepp_kernel (tournament-pivoting panel)", "latency-bound"),
+        "pmchwt_singular": ("alu", 1.0, None, "pmchwt_singular_kernel (FP64 Sauter-Schwab)",
+                            "work = touching pairs per launch"),
+    }
+    dom = max((f for f in model if fam_stats[f]["ms_per_step"] > 0), key=lambda f: fam_stats[f]["ms_per_step"])
+    bound, wsc, peak, kname, note = model[dom]
+    st = fam_stats[dom]
+    achieved = st["work_per_step"] * wsc / (st["ms_per_step"] * 1e-3) / 1e12
+    roofline = {"bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 3) if peak else None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
+                "kernel": kname, "family": dom, "ms_per_step": round(st["ms_per_step"], 2),
+                "launches_per_step": st["launches_per_step"], "peak_source": note}
+    families_out = {f: {"ms_per_step": round(v["ms_per_step"], 2), "launches_per_step": v["launches_per_step"]}
+                    for f, v in fam_stats.items() if v["ms_per_step"] > 0}
+    if rank != 0:
+        return
+    e2e = None
+    if not args.no_e2e:
+        # the public API from host arrays: mesh upload, the step, the far field downloaded
+        h2d = sm.verts.nbytes + sm.tris.nbytes + sm.vnormals.nbytes + inc.nbytes
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2 = F.mesh_create(sm.verts, sm.tris, sm.vnormals)
+            step(m2, F.MIXED)
+            Fh = out.cpu().numpy()
+            ts.append(time.perf_counter() - t0)
+            del m2
+        e2e = {"value": round(statistics.median(ts), 4), "unit": "s per PMCHWT step", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(Fh.nbytes), "steps": 3, "stat": "median"}
+    fp64 = None
+    if not args.no_fp64:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(mesh, F.FP64)
+        e1.record()
+        torch.cuda.synchronize()
+        F64 = out.cpu().numpy()[:, 0]
+        fp64 = {"s_per_step": round(e0.elapsed_time(e1) / 1e3, 3),
+                "rel_diff_farfield_mixed_vs_fp64": float(np.linalg.norm(F_mixed - F64) / np.linalg.norm(F64)),
+                "speedup_mixed_vs_fp64": round(e0.elapsed_time(e1) / ms, 2)}
+    R = np.array([[0, 0, 1.0], [0, -1.0, 0], [1.0, 0, 0]])  # (e_x, e_y, e_z) -> (e_z, -e_y, e_x)
+    import oracle.mie as mie
+
+    Fm = (mie.farfield(W["k"], 1.0, dirs @ R, eps_r=W["eps_r"], mu_r=W["mu_r"]) @ R.T).reshape(-1)
+    t_asm = phase.get("assemble", 0.0)
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per PMCHWT step", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: f64 assembly, 3xTF32 tensor-core LU (c64 factors) with FP64-class refinement",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "triangles": sm.nt, "N": N, "unknowns": 2 * N, "k0": W["k"],
+                       "eps_r": W["eps_r"], "mu_r": W["mu_r"], "n_dir": W["n_dir"], "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (Z is 3.8 GB)"},
+            "median_step_ms": round(statistics.median(step_ms), 2),
+            "entries_per_s": round(4.0 * N * N / (t_asm * 1e-3), 1) if t_asm > 0 else None,
+            "phase_ms": phase, "families": families_out, "ir_backward_error": berr,
+            "rel_err_farfield_vs_mie": float(np.linalg.norm(F_mixed - Fm) / np.linalg.norm(Fm)),
+            "roofline": roofline, "peaks_microbench_tflops": upeaks, "gpu_launches": launches, "clocks": clk,
+            "e2e": e2e, "fp64": fp64}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        lo = W["oracle_level"]
+        om = O.from_synth(S.icosphere(lo))
+        t0 = time.perf_counter()
+        Zo = O.assemble_pmchwt(om, W["k"], W["eps_r"], W["mu_r"])
+        bo = O.rhs_pmchwt(om, W["k"], [W["d"]], [W["p"]])
+        t1 = time.perf_counter()
+        xo = O.solve(Zo, bo)
+        t2 = time.perf_counter()
+        O.farfield_matrix_pmchwt(om, W["k"], dirs) @ xo
+        t3 = time.perf_counter()
+        T_ratio = sm.nt / om.nt
+        model_s = (t1 - t0) * T_ratio**2 + (t2 - t1) * T_ratio**3 + (t3 - t2) * T_ratio
+        line["cpu_baseline"] = {
+            "value": round(model_s, 2), "unit": "s per PMCHWT step", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": f"the complete oracle step on the {om.nt}-triangle sphere (2N = {2 * om.n_edges}) measured: "
+                      f"assembly {t1 - t0:.2f} s, LAPACK solve {t2 - t1:.2f} s, far field {t3 - t2:.2f} s; scaled "
+                      f"to {sm.nt} triangles by the exact operation counts (pairs x{T_ratio**2:.0f}, LU "
+                      f"x{T_ratio**3:.0f}, far field x{T_ratio:.0f})",
+            "measured_level_s": round(t3 - t0, 2)}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batched(W):
     """The FP64 CPU oracle, as it stands, on the batched workload: assembly, plane-wave
     right-hand sides and the LAPACK solve of all 16 directions, measured for every
@@ -978,7 +1184,7 @@ def main():
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     kind = WORKLOADS[args.workload].get("kind")
     if args.impl == "reference":
-        if kind in ("mc", "lowrank"):
+        if kind in ("mc", "lowrank", "pmchwt"):
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the default workload; "
                               "this workload reports its oracle baseline in its own line"}))
         else:
@@ -989,6 +1195,8 @@ def main():
         run_mc(args)
     elif kind == "lowrank":
         run_lowrank(args)
+    elif kind == "pmchwt":
+        run_pmchwt(args)
     else:
         run_fosb(args)
 

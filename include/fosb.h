@@ -273,6 +273,45 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
                                   const void* X, int64_t ldx, int64_t ncols, double weight, int hermitian_mirror,
                                   int pseudo, int prec, void* out, int64_t ldo, int accumulate, void* stream);
 
+/* ---- Dielectric scatterer: the PMCHWT system (Section II-C eq. pmchwt) --------------
+ * fosb_assemble_pmchwt: Galerkin matrix of A_0 + A^_1 (multitrace operators of eq.
+ * BOmultitraceA, A_k = [[K_k, T_k], [-T_k, K_k]] and its eta-scaled form) for the exterior
+ * Cauchy data (j, m) = (gamma_D^c E, gamma_N^c E) of the total field, tested with the
+ * x-pairing against RWG functions:
+ *     Z (2N x 2N) = [[K_0 + K_1, T_0 + eta T_1], [-T_0 - T_1/eta, K_0 + K_1]],
+ *     T_k[m, n] = -[ik int int G f_m.f_n + 1/(ik) int int G div f_m div f_n]   (EFIO, as above),
+ *     K_k[m, n] = -int int (x - y).(f_n(y) x f_m(x)) exp(ikr)(ikr - 1)/(4 pi r^3)  (MFIO
+ *                 K_k = {gamma_D H_k}, Section II-B),
+ * k = k0 outside, k1 = k0 sqrt(eps_r mu_r) inside, eta = sqrt(mu_r/eps_r) (eq.
+ * relativeParameters).  The right-hand side is the tested incident Cauchy data,
+ *     b[m, s] = -int E_inc_s . f_m,   b[N + m, s] = -int (d_s x p_s) exp(ik0 d_s.x) . f_m,
+ * which with the incident field's Calderon identity is the printed system
+ * (A_0 + A^_1) xi_sc = (I/2 - A^_1) xi_inc for xi_sc = (j, m) - xi_inc.
+ * Regular pairs: the 6-point rule in x and y, FP64; touching pairs: Sauter-Schwab with
+ * opts->n_ss points per coordinate (identical pairs add nothing to K_k on a flat triangle).
+ *   eps_r, mu_r : relative permittivity and permeability (finite, > 0; lossless media)
+ *   opts        : NULL or n_ss with arith = FOSB_ASM_FP64 (the only arithmetic offered)
+ *   Z           : device, 2N x 2N complex128, leading dimension ldz >= 2N; overwritten
+ *   inc         : host, n_inc x 9 as for fosb_assemble_efie (d, Re p, Im p)
+ *   b           : device, 2N x n_inc complex128 (ldb >= n_inc) or NULL when n_inc = 0
+ * Z is not complex symmetric; factor it with fosb_factor (FOSB_FP64 or FOSB_MIXED) and
+ * solve with fosb_solve (op = 'N').  Enqueued on `stream` without synchronising it.
+ * Errors: FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_assemble_pmchwt(fosb_mesh mesh, double k0, double eps_r, double mu_r, const fosb_quad_opts* opts,
+                                 void* Z, int64_t ldz, const double* inc, int64_t n_inc, void* b, int64_t ldb,
+                                 void* stream);
+
+/* fosb_farfield_pmchwt: out (3 n_dir x ncols, ldo) = weight * A X (+ out if accumulate),
+ * X (2N x ncols, ldx) exterior Cauchy data (j on rows 0..N-1, m on rows N..2N-1), with the
+ * far field of E_sc = -E_k0 m - H_k0 j (Section II-C, E = E_inc + R(xi), R = (-H, -E)):
+ *     F(xh) = -ik0 [xh x sum_n j_n v_n + (I - xh xh^T) sum_n m_n v_n],
+ *     v_n = int f_n(y) exp(-ik0 xh.y) dy (6-point rule), row 3d + c = component c at xh_d.
+ * dirs: host n_dir x 3 unit vectors.  complex128 throughout; synchronises `stream`.
+ * Errors: FOSB_ERR_INVALID_ARG. */
+fosb_status fosb_farfield_pmchwt(fosb_mesh mesh, double k0, const double* dirs, int64_t n_dir, const void* X,
+                                 int64_t ldx, int64_t ncols, double weight, void* out, int64_t ldo, int accumulate,
+                                 void* stream);
+
 /* ---- Low-rank right-hand side of the tensor equations (Section VI, further work (ii)) ----
  * fosb_kernel_lowrank: pivoted Cholesky factorisation K ~ R^T R (Harbrecht, Peters and
  * Schneider 2012) of the covariance kernel matrix K_pq = sigma^2 rho(|x_p - x_q|) over the

@@ -264,6 +264,22 @@ def assemble_pmchwt(mesh: RWGMesh, k0: float, eps_r: float, mu_r: float, n_ss: i
     return Z
 
 
+def pmchwt_entries(mesh: RWGMesh, k0: float, eps_r: float, mu_r: float, rows, cols, n_ss: int = 5,
+                   threads: int | None = None) -> np.ndarray:
+    """Selected entries of assemble_pmchwt's matrix, computed one by one (large-N samples)."""
+    k1, eta = dielectric_wavenumbers(k0, eps_r, mu_r)
+    qb, qw = triangle_rule6()
+    gx, gw = gauss_legendre01(n_ss)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.zeros(rows.shape[0], dtype=np.complex128)
+    _load().orc_pmchwt_entries(*mesh._args(), _p(mesh.edge_tris), ctypes.c_int64(mesh.n_edges), ctypes.c_double(k0),
+                               ctypes.c_double(k1), ctypes.c_double(eta), _p(qb), _p(qw), ctypes.c_int(6), _p(gx),
+                               _p(gw), ctypes.c_int(n_ss), _p(rows), _p(cols), ctypes.c_int64(rows.shape[0]), _p(out),
+                               ctypes.c_int(threads or n_threads()))
+    return out
+
+
 def rhs_pmchwt(mesh: RWGMesh, k0: float, d, p) -> np.ndarray:
     """Tested incident Cauchy data (2N x n_inc): <gamma_D E_inc, f_m>_x = -int E_inc . f_m on
     top and <gamma_N E_inc, f_m>_x = -int (curl E_inc/(ik0)) . f_m below; for

@@ -571,6 +571,51 @@ int orc_assemble_mfio(const double* verts, const int32_t* tris, int64_t nt, cons
   return 0;
 }
 
+// Selected entries Z[rows[e], cols[e]] of the 2N x 2N PMCHWT matrix (orc_assemble_pmchwt),
+// each from the four triangle-pair blocks of its two edges, for large-N parity samples.
+int orc_pmchwt_entries(const double* verts, const int32_t* tris, int64_t nt, const int32_t* tri_edge,
+                       const double* tri_sign, const double* edge_len, const int32_t* edge_tris, int64_t n_edges,
+                       double k0, double k1, double eta, const double* qb, const double* qw, int nq,
+                       const double* glx, const double* glw, int nss, const int64_t* rows, const int64_t* cols,
+                       int64_t count, double* out, int nthreads) {
+  MeshView m{verts, tris, nt, tri_edge, tri_sign, edge_len};
+  Rules q{qb, qw, nq, glx, glw, nss};
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t e = 0; e < count; ++e) {
+    const int br = rows[e] >= n_edges, bc = cols[e] >= n_edges;
+    const int64_t r = rows[e] - br * n_edges, c = cols[e] - bc * n_edges;
+    cplx T0 = 0.0, T1 = 0.0, K0 = 0.0, K1 = 0.0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        int64_t t1 = edge_tris[2 * r + a], t2 = edge_tris[2 * c + b];
+        int i = -1, j = -1;
+        for (int s = 0; s < 3; ++s) {
+          if (tri_edge[3 * t1 + s] == r) i = s;
+          if (tri_edge[3 * t2 + s] == c) j = s;
+        }
+        cplx blk[3][3];
+        if (br == bc) {
+          pair_block_mfio(m, q, k0, t1, t2, blk);
+          K0 += blk[i][j];
+          pair_block_mfio(m, q, k1, t1, t2, blk);
+          K1 += blk[i][j];
+        } else {
+          pair_block(m, q, k0, t1, t2, blk);
+          T0 += blk[i][j];
+          pair_block(m, q, k1, t1, t2, blk);
+          T1 += blk[i][j];
+        }
+      }
+    cplx v = br == bc ? K0 + K1 : (br == 0 ? T0 + eta * T1 : -T0 - T1 / eta);
+    out[2 * e] = v.real();
+    out[2 * e + 1] = v.imag();
+  }
+  return 0;
+}
+
 // One 3 x 3 MFIO block (t1 test, t2 trial) for the oracle's pins.
 int orc_mfio_block(const double* verts, const int32_t* tris, int64_t nt, const int32_t* tri_edge,
                    const double* tri_sign, const double* edge_len, double k, const double* qb, const double* qw, int nq,

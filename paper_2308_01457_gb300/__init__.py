@@ -76,7 +76,7 @@ def lib():
                      "fosb_debug_set_wait_limit", "fosb_peak_microbench", "fosb_assemble_efie_batched",
                      "fosb_solve_batched", "fosb_field_samples", "fosb_mesh_perturb", "fosb_mc_moments",
                      "fosb_zgemm_fp64class", "fosb_kernel_lowrank", "fosb_covariance_lowrank",
-                     "fosb_lowrank_combine"):
+                     "fosb_lowrank_combine", "fosb_assemble_pmchwt", "fosb_farfield_pmchwt"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -293,6 +293,32 @@ def farfield_moments(m1: Mesh, k: float, dirs, X, out, m2: Mesh | None = None, w
                                        ctypes.c_double(weight), ctypes.c_int(int(mirror)), ctypes.c_int(int(pseudo)),
                                        ctypes.c_int(prec), _ptr(out), ctypes.c_int64(1 if out.dim() == 1 else _ld(out)),
                                        ctypes.c_int(int(accumulate)), _stream(stream)))
+    return out
+
+
+def assemble_pmchwt(mesh: Mesh, k0: float, eps_r: float, mu_r: float, Z, inc=None, b=None, n_ss: int = 5,
+                    stream=None):
+    """fosb_assemble_pmchwt: the dielectric scatterer's PMCHWT matrix Z (2N x 2N complex128)
+    and, if inc is given, the tested incident Cauchy data b (2N x n_inc)."""
+    opts = QuadOpts(n_ss, ASM_FP64)
+    inc_a = None if inc is None else _np(inc, np.float64).reshape(-1, 9)
+    n_inc = 0 if inc_a is None else inc_a.shape[0]
+    _check(lib().fosb_assemble_pmchwt(mesh.handle, ctypes.c_double(k0), ctypes.c_double(eps_r), ctypes.c_double(mu_r),
+                                      ctypes.byref(opts), _ptr(Z), ctypes.c_int64(_ld(Z)),
+                                      None if inc_a is None else inc_a.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.c_int64(n_inc), None if b is None else _ptr(b),
+                                      ctypes.c_int64(_ld(b) if b is not None else 0), _stream(stream)))
+
+
+def farfield_pmchwt(mesh: Mesh, k0: float, dirs, X, out, weight: float = 1.0, accumulate: bool = False, stream=None):
+    """fosb_farfield_pmchwt: out (3 n_dir x ncols) = w A X for exterior Cauchy data X (2N x ncols)."""
+    d = _np(dirs, np.float64).reshape(-1, 3)
+    ncols = 1 if X.dim() == 1 else X.shape[1]
+    _check(lib().fosb_farfield_pmchwt(mesh.handle, ctypes.c_double(k0), d.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.c_int64(d.shape[0]), _ptr(X), ctypes.c_int64(1 if X.dim() == 1 else _ld(X)),
+                                      ctypes.c_int64(ncols), ctypes.c_double(weight), _ptr(out),
+                                      ctypes.c_int64(1 if out.dim() == 1 else _ld(out)), ctypes.c_int(int(accumulate)),
+                                      _stream(stream)))
     return out
 
 

@@ -24,6 +24,7 @@ fosb_status ensure_rules(int nss) {
     upload_rules(r);
     upload_rules_adjoint(r);
     upload_rules_ff(r);
+    upload_rules_pmchwt(r);
     FOSB_CUDA(cudaDeviceSynchronize());
     g_rules_nss[dev] = nss;
   }

@@ -155,6 +155,7 @@ cudaError_t launch_rhs(const DevMesh& m, double k, const double* d_inc, int64_t 
 void upload_rules(const Rules& r);
 void upload_rules_adjoint(const Rules& r);
 void upload_rules_ff(const Rules& r);
+void upload_rules_pmchwt(const Rules& r);
 double ff_max_phase();  // k * mesh diameter must stay below this for the float-float kernel
 // Adjoint shape gradients (see adjoint.cu): grad (V x 3) += -grad Re sum_i lam_i^T Z u_i, and
 // += grad Re J_P for plane-wave moments with per-column parameters d_pw (ncols x 11:
