@@ -702,6 +702,7 @@ def run_pmchwt(args):
     dirs = S.zplane_directions(W["n_dir"])
     inc = F.incidence([W["d"]], [W["p"]])
     upeaks = {kd: round(F.peak_microbench(kd), 2) for kd in ("fp32", "fp64", "tf32", "bf16")}
+    arith = F.ASM_FF if args.arith == "ff" else F.ASM_FP64
     mesh = F.mesh_create(sm.verts, sm.tris, sm.vnormals)
     N = mesh.n_edges
     C128 = torch.complex128
@@ -713,7 +714,7 @@ def run_pmchwt(args):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if timers is not None else None
         if ev:
             ev[0].record()
-        F.assemble_pmchwt(m, W["k"], W["eps_r"], W["mu_r"], Z, inc=inc, b=b)
+        F.assemble_pmchwt(m, W["k"], W["eps_r"], W["mu_r"], Z, inc=inc, b=b, arith=arith)
         if ev:
             ev[1].record()
         lu = F.factor(Z, prec=prec)
@@ -774,10 +775,12 @@ def run_pmchwt(args):
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     tf32_peak = bf16 * TF32_PER_BF16
     model = {
-        "pmchwt_regular": ("alu", PMCHWT_OPS_PER_POINT_PAIR, upeaks["fp64"], "pmchwt_regular_kernel (FP64)",
-                           f"{PMCHWT_OPS_PER_POINT_PAIR:.0f} algorithmic FP64 ops per point pair and wavenumber "
-                           "(work = point pairs of both launches); peak = the FP64 FMA pipe measured by "
-                           "fosb_peak_microbench"),
+        "pmchwt_regular": ("alu", PMCHWT_OPS_PER_POINT_PAIR, upeaks["fp32" if arith == F.ASM_FF else "fp64"],
+                           "pmchwt_regular_ff_kernel (float-float)" if arith == F.ASM_FF
+                           else "pmchwt_regular_kernel (FP64)",
+                           f"{PMCHWT_OPS_PER_POINT_PAIR:.0f} algorithmic FP64-class ops per point pair and "
+                           "wavenumber (work = point pairs of both launches); peak = the FP32 (float-float) or FP64 "
+                           "FMA pipe measured by fosb_peak_microbench"),
         "lu_update": ("tensor", 1.0, tf32_peak, "cgemm_update_split_kernel (tcgen05 kind::tf32, 3xTF32 complex)",
                       "TF32 dense = measured bf16 sustained x 1.1/2.25; work = useful complex flops 8MNK"),
         "lu_panel": ("latency", 1.0, None, "tslu_gepp_kernel (tournament-pivoting panel)", "latency-bound"),
@@ -831,10 +834,12 @@ def run_pmchwt(args):
     line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per PMCHWT step", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "mixed: f64 assembly, 3xTF32 tensor-core LU (c64 factors) with FP64-class refinement",
+            "dtype": ("mixed: float-float (f32x2) regular pairs, f64 singular pairs" if arith == F.ASM_FF
+                      else "mixed: f64 assembly") + ", 3xTF32 tensor-core LU (c64 factors) with FP64-class refinement",
             "data": "synthetic",
             "config": {"workload": args.workload, "triangles": sm.nt, "N": N, "unknowns": 2 * N, "k0": W["k"],
-                       "eps_r": W["eps_r"], "mu_r": W["mu_r"], "n_dir": W["n_dir"], "parallelism": f"replicas{ws}",
+                       "eps_r": W["eps_r"], "mu_r": W["mu_r"], "n_dir": W["n_dir"], "assembly": args.arith,
+                       "parallelism": f"replicas{ws}",
                        "l2": "inputs larger than L2 (Z is 3.8 GB)"},
             "median_step_ms": round(statistics.median(step_ms), 2),
             "entries_per_s": round(4.0 * N * N / (t_asm * 1e-3), 1) if t_asm > 0 else None,

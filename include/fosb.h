@@ -287,10 +287,12 @@ fosb_status fosb_farfield_moments(fosb_mesh m1, fosb_mesh m2, double k, const do
  *     b[m, s] = -int E_inc_s . f_m,   b[N + m, s] = -int (d_s x p_s) exp(ik0 d_s.x) . f_m,
  * which with the incident field's Calderon identity is the printed system
  * (A_0 + A^_1) xi_sc = (I/2 - A^_1) xi_inc for xi_sc = (j, m) - xi_inc.
- * Regular pairs: the 6-point rule in x and y, FP64; touching pairs: Sauter-Schwab with
- * opts->n_ss points per coordinate (identical pairs add nothing to K_k on a flat triangle).
+ * Regular pairs: the 6-point rule in x and y in FP64 or float-float (opts->arith; both
+ * wavenumbers must keep k * mesh diameter below the float-float phase range, 48); touching
+ * pairs: Sauter-Schwab in FP64 with opts->n_ss points per coordinate (identical pairs add
+ * nothing to K_k on a flat triangle).
  *   eps_r, mu_r : relative permittivity and permeability (finite, > 0; lossless media)
- *   opts        : NULL or n_ss with arith = FOSB_ASM_FP64 (the only arithmetic offered)
+ *   opts        : NULL (n_ss = 5, FP64) or n_ss with arith = FOSB_ASM_FP64 or FOSB_ASM_FF
  *   Z           : device, 2N x 2N complex128, leading dimension ldz >= 2N; overwritten
  *   inc         : host, n_inc x 9 as for fosb_assemble_efie (d, Re p, Im p)
  *   b           : device, 2N x n_inc complex128 (ldb >= n_inc) or NULL when n_inc = 0

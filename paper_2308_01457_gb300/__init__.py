@@ -297,10 +297,11 @@ def farfield_moments(m1: Mesh, k: float, dirs, X, out, m2: Mesh | None = None, w
 
 
 def assemble_pmchwt(mesh: Mesh, k0: float, eps_r: float, mu_r: float, Z, inc=None, b=None, n_ss: int = 5,
-                    stream=None):
+                    arith: int = ASM_FP64, stream=None):
     """fosb_assemble_pmchwt: the dielectric scatterer's PMCHWT matrix Z (2N x 2N complex128)
-    and, if inc is given, the tested incident Cauchy data b (2N x n_inc)."""
-    opts = QuadOpts(n_ss, ASM_FP64)
+    and, if inc is given, the tested incident Cauchy data b (2N x n_inc); regular pairs in
+    FP64 (ASM_FP64) or float-float (ASM_FF)."""
+    opts = QuadOpts(n_ss, arith)
     inc_a = None if inc is None else _np(inc, np.float64).reshape(-1, 9)
     n_inc = 0 if inc_a is None else inc_a.shape[0]
     _check(lib().fosb_assemble_pmchwt(mesh.handle, ctypes.c_double(k0), ctypes.c_double(eps_r), ctypes.c_double(mu_r),

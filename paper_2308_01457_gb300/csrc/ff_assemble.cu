@@ -132,8 +132,15 @@ __device__ __forceinline__ void expi_ff(ff theta, const FFConst& C, const float 
 
 // One regular point pair block: test triangle t1, trial triangle t2 (t1, t2 < m.nt); adds the
 // 3 x 3 RWG block into Z unless the triangles touch.  tab: the sin/cos table in shared memory.
-__device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst& C, double* Z, int64_t ldz,
-                                                int64_t t1, int64_t t2, const float (*tab)[4]) {
+// MFIO: also the block of the MFIO of the dielectric (PMCHWT) system, into ZK (same ldz):
+//   K_ij = -int int (x - y).(f_j(y) x f_i(x)) g,  g = exp(ikr)(ikr - 1)/(4 pi r^3).
+// With a = x - p_i, b = y - q_j, (x - y).(b x a) = (p_i - q_j).(b x a) is bilinear in the
+// barycentric coordinates, so the pair's second moment matrix
+//   nu_ab = sum_pq w_p w_q lambda_pa beta_qb exp(ikr)(ikr - 1)/r^3
+// gives K_ij = -(s_i l_i s'_j l'_j / (16 pi)) sum_ab nu_ab (p_i - q_j).((Q_b - q_j) x (P_a - p_i)).
+template <bool MFIO>
+__device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst& C, double* Z, double* ZK,
+                                                int64_t ldz, int64_t t1, int64_t t2, const float (*tab)[4]) {
   const int64_t nt = m.nt;
   int v1[3], v2[3];
 #pragma unroll
@@ -151,19 +158,29 @@ __device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst&
   ff D[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) D[c] = ff_add(ldff(F, nt, 36 + 2 * c, t1), ff_neg(ldff(F, nt, 36 + 2 * c, t2)));
-  CFF mu[3][3];
+  CFF mu[3][3], nu[MFIO ? 3 : 1][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) mu[a][b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
+  if constexpr (MFIO) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) nu[a][b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
+  }
 #pragma unroll 1
   for (int p = 0; p < 6; ++p) {
     ff E[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) E[c] = ff_add(D[c], ldff(F, nt, (p * 3 + c) * 2, t1));
-    CFF A[3];
+    CFF A[3], B[MFIO ? 3 : 1];
 #pragma unroll
     for (int b = 0; b < 3; ++b) A[b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
+    if constexpr (MFIO) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) B[b] = CFF{{0.f, 0.f}, {0.f, 0.f}};
+    }
     // two point pairs per iteration: enough independent work per warp, a third of the code
     // of a full unroll (instruction fetch bounded the fully unrolled loop)
 #pragma unroll 2
@@ -180,13 +197,26 @@ __device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst&
       const float corr = ((1.0f - rq.h) - rq.l) * y0;    // 1 - rq.h exact (rq.h ~ 1)
       const ff rinv = fast_two_sum(y0, corr);
       ff cs, sn;
-      expi_ff(ff_mul(C.k, r), C, tab, cs, sn);
+      const ff kr = ff_mul(C.k, r);
+      expi_ff(kr, C, tab, cs, sn);
       const CFF G = {ff_mul(cs, rinv), ff_mul(sn, rinv)};
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const ff wb = {c_wb[q][b][0], c_wb[q][b][1]};
         acc_mul(A[b].r, G.r, wb);
         acc_mul(A[b].i, G.i, wb);
+      }
+      if constexpr (MFIO) {
+        // g = G (ikr - 1) / r^2: Re = -(G.r + G.i kr) / r^2, Im = (G.r kr - G.i) / r^2
+        const ff rinv2 = ff_sqr(rinv);
+        const CFF g = {ff_neg(ff_mul(ff_add(G.r, ff_mul(G.i, kr)), rinv2)),
+                       ff_mul(ff_add(ff_mul(G.r, kr), ff_neg(G.i)), rinv2)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const ff wb = {c_wb[q][b][0], c_wb[q][b][1]};
+          acc_mul(B[b].r, g.r, wb);
+          acc_mul(B[b].i, g.i, wb);
+        }
       }
     }
 #pragma unroll
@@ -201,6 +231,22 @@ __device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst&
       for (int b = 0; b < 3; ++b) {
         acc_mul(mu[a][b].r, A[b].r, wa);
         acc_mul(mu[a][b].i, A[b].i, wa);
+      }
+    }
+    if constexpr (MFIO) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        B[b].r = norm(B[b].r);
+        B[b].i = norm(B[b].i);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const ff wa = {c_wb[p][a][0], c_wb[p][a][1]};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          acc_mul(nu[a][b].r, B[b].r, wa);
+          acc_mul(nu[a][b].i, B[b].i, wa);
+        }
       }
     }
   }
@@ -278,6 +324,70 @@ __device__ __forceinline__ void regular_ff_pair(const DevMesh& m, const FFConst&
       atomicAdd(dst + 1, to_d(ff_mul(sig, zi)));
     }
   }
+  if constexpr (MFIO) {
+    // X[be][al] = eQ_be x eP_al;  (P_a - p_i) = eP_i (a = i+1), -eP_{i+2} (a = i+2), and the same for Q
+    ff X[3][3][3];
+#pragma unroll
+    for (int be = 0; be < 3; ++be)
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+          X[be][al][c] = ff_add(ff_mul(eQ[be][c1], eP[al][c2]), ff_neg(ff_mul(eQ[be][c2], eP[al][c1])));
+        }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        nu[a][b].r = norm(nu[a][b].r);
+        nu[a][b].i = norm(nu[a][b].i);
+      }
+    const ff zero = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int a1 = (i + 1) % 3, a2 = (i + 2) % 3;
+      // p_i - P_0 (vertex i relative to vertex 0 of t1)
+      ff pi_[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pi_[c] = i == 0 ? zero : (i == 1 ? P1[c] : P2[c]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int b1 = (j + 1) % 3, b2 = (j + 2) % 3;
+        // d = p_i - q_j = (P_0 - Q_0) + (p_i - P_0) - (q_j - Q_0)
+        ff d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const ff qj = j == 0 ? zero : (j == 1 ? Q1[c] : Q2[c]);
+          d[c] = ff_add(ff_add(D[c], pi_[c]), ff_neg(qj));
+        }
+        auto dot3 = [&](const ff (&x)[3]) {
+          ff r = ff_mul(d[0], x[0]);
+          r = ff_add(r, ff_mul(d[1], x[1]));
+          return ff_add(r, ff_mul(d[2], x[2]));
+        };
+        // (a, b) = (a1, b1), (a1, b2), (a2, b1), (a2, b2)
+        const ff t[4] = {dot3(X[j][i]), ff_neg(dot3(X[b2][i])), ff_neg(dot3(X[j][a2])), dot3(X[b2][a2])};
+        CFF V = {{0.f, 0.f}, {0.f, 0.f}};
+        acc_mul(V.r, nu[a1][b1].r, t[0]);
+        acc_mul(V.i, nu[a1][b1].i, t[0]);
+        acc_mul(V.r, nu[a1][b2].r, t[1]);
+        acc_mul(V.i, nu[a1][b2].i, t[1]);
+        acc_mul(V.r, nu[a2][b1].r, t[2]);
+        acc_mul(V.i, nu[a2][b1].i, t[2]);
+        acc_mul(V.r, nu[a2][b2].r, t[3]);
+        acc_mul(V.i, nu[a2][b2].i, t[3]);
+        V.r = norm(V.r);
+        V.i = norm(V.i);
+        // K_ij = -(s_i l_i s'_j l'_j / (16 pi)) V
+        const ff sig = ff_mul(ff_mul(sl1[i], sl2[j]), C.inv4pi);
+        const float q4 = -0.25f;
+        double* dst = ZK + 2 * (int64_t(e1[i]) * ldz + e2[j]);
+        atomicAdd(dst, to_d(ff_mul(sig, V.r)) * q4);
+        atomicAdd(dst + 1, to_d(ff_mul(sig, V.i)) * q4);
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst C, double* Z, int64_t ldz) {
@@ -287,7 +397,19 @@ __global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst
   const int64_t t1 = int64_t(blockIdx.y) * 4 + (threadIdx.x >> 5);
   const int64_t t2 = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
   if (t1 >= m.nt || t2 >= m.nt) return;
-  regular_ff_pair(m, C, Z, ldz, t1, t2, tab);
+  regular_ff_pair<false>(m, C, Z, nullptr, ldz, t1, t2, tab);
+}
+
+// Dielectric (PMCHWT) system: the EFIO block into ZT and the MFIO block into ZK.
+__global__ void __launch_bounds__(128) pmchwt_regular_ff_kernel(DevMesh m, FFConst C, double* ZT, double* ZK,
+                                                                int64_t ldz) {
+  __shared__ float tab[128][4];
+  for (int e = threadIdx.x; e < 128 * 4; e += blockDim.x) tab[e >> 2][e & 3] = c_sctab[e >> 2][e & 3];
+  __syncthreads();
+  const int64_t t1 = int64_t(blockIdx.y) * 4 + (threadIdx.x >> 5);
+  const int64_t t2 = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
+  if (t1 >= m.nt || t2 >= m.nt) return;
+  regular_ff_pair<true>(m, C, ZT, ZK, ldz, t1, t2, tab);
 }
 
 // Batched form: one persistent launch over the tiles of many meshes.  Tile w of the batch
@@ -341,7 +463,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) efie_regular_ff_batched_kern
     const int64_t local = w - s_item.tile_start;
     const int64_t ty = local / s_item.tiles_x, tx = local - ty * s_item.tiles_x;
     const int64_t t1 = ty * WARPS + (threadIdx.x >> 5), t2 = tx * 32 + (threadIdx.x & 31);
-    if (t1 < s_item.m.nt && t2 < s_item.m.nt) regular_ff_pair(s_item.m, s_item.C, s_item.Z, s_item.ldz, t1, t2, tab);
+    if (t1 < s_item.m.nt && t2 < s_item.m.nt)
+      regular_ff_pair<false>(s_item.m, s_item.C, s_item.Z, nullptr, s_item.ldz, t1, t2, tab);
     __syncthreads();  // s_tile / s_item are rewritten by the next ticket
   }
 }
@@ -408,6 +531,17 @@ cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_
   dim3 grid(cdiv(m.nt, 32), cdiv(m.nt, 4));
   if (grid.y > 65535u) return cudaErrorInvalidValue;
   efie_regular_ff_kernel<<<grid, 128, 0, s>>>(m, C, Z, ldz);
+  return launched();
+}
+
+// PMCHWT regular pairs for one wavenumber: EFIO blocks into ZT, MFIO blocks into ZK (FP64
+// atomics; both N x N blocks of the 2N x 2N matrix with leading dimension ldz).
+cudaError_t launch_pmchwt_regular_ff(const DevMesh& m, double k, double* ZT, double* ZK, int64_t ldz, cudaStream_t s) {
+  if (k * m.diameter >= ff_max_phase()) return cudaErrorInvalidValue;
+  const FFConst C = make_ff_const(k);
+  dim3 grid(cdiv(m.nt, 32), cdiv(m.nt, 4));
+  if (grid.y > 65535u) return cudaErrorInvalidValue;
+  pmchwt_regular_ff_kernel<<<grid, 128, 0, s>>>(m, C, ZT, ZK, ldz);
   return launched();
 }
 

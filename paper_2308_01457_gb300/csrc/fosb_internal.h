@@ -165,6 +165,8 @@ cudaError_t launch_adjoint_pairs(const DevMesh& m, double k, int nss, const doub
 cudaError_t launch_adjoint_planewave(const DevMesh& m, double k, int64_t ncols, const double* d_pw, const double* wgt,
                                      int64_t ldw, double* grad, cudaStream_t s);
 cudaError_t launch_efie_regular_ff(const DevMesh& m, double k, double* Z, int64_t ldz, cudaStream_t s);
+// PMCHWT regular pairs in float-float for one wavenumber: EFIO blocks into ZT, MFIO blocks into ZK.
+cudaError_t launch_pmchwt_regular_ff(const DevMesh& m, double k, double* ZT, double* ZK, int64_t ldz, cudaStream_t s);
 
 // Far field
 cudaError_t launch_farfield_matrix(const DevMesh& m, double k, const double* d_dirs, int64_t n_dir, bool fp32,

@@ -31,6 +31,7 @@
 // add nothing to K (the principal value of the averaged trace).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -424,13 +425,18 @@ __global__ void pmchwt_farfield_kernel(DevMesh m, double k, const double* dirs, 
 
 inline unsigned pm_blocks(int64_t n, int bs) { return unsigned((n + bs - 1) / bs); }
 
-cudaError_t assemble_pmchwt_one_k(const DevMesh& d, double k, int nss, double* ZT, double* ZK, int64_t ldz,
-                                  cudaStream_t s) {
+cudaError_t assemble_pmchwt_one_k(const DevMesh& d, double k, int nss, int arith, double* ZT, double* ZK,
+                                  int64_t ldz, cudaStream_t s) {
   {
     ProfScope prof("pmchwt_regular", s, 36.0 * (double(d.nt) * double(d.nt) - double(2 * d.ntouch - d.nt)));
-    dim3 grid(pm_blocks(d.nt, 32), pm_blocks(d.nt, 8));
-    pmchwt_regular_kernel<<<grid, 256, 0, s>>>(d, k, ZT, ZK, ldz);
-    cudaError_t e = launched();
+    cudaError_t e;
+    if (arith == FOSB_ASM_FF) {
+      e = launch_pmchwt_regular_ff(d, k, ZT, ZK, ldz, s);
+    } else {
+      dim3 grid(pm_blocks(d.nt, 32), pm_blocks(d.nt, 8));
+      pmchwt_regular_kernel<<<grid, 256, 0, s>>>(d, k, ZT, ZK, ldz);
+      e = launched();
+    }
     if (e != cudaSuccess) return e;
   }
   if (d.ntouch == 0) return cudaSuccess;
@@ -467,22 +473,28 @@ fosb_status fosb_assemble_pmchwt(fosb_mesh mesh, double k0, double eps_r, double
     return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: bad incidence arguments");
   const int nss = opts && opts->n_ss > 0 ? opts->n_ss : 5;
   if (nss > 12) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: n_ss must be in 1..12");
-  if (opts && opts->arith != FOSB_ASM_FP64)
-    return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: only FOSB_ASM_FP64 regular pairs are supported");
-  if (mesh->d.nt > int64_t(65535) * 8) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: too many triangles");
+  const int arith = opts ? opts->arith : FOSB_ASM_FP64;
+  if (arith != FOSB_ASM_FP64 && arith != FOSB_ASM_FF)
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: arith must be FOSB_ASM_FP64 or FOSB_ASM_FF");
+  if (mesh->d.nt > int64_t(65535) * 4) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: too many triangles");
   for (int64_t s = 0; s < n_inc; ++s)
     for (int c = 0; c < 9; ++c)
       if (!std::isfinite(inc[9 * s + c])) return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: non-finite incidence");
   FOSB_TRY(ensure_rules_for(nss));
   const double k1 = k0 * std::sqrt(eps_r * mu_r), eta = std::sqrt(mu_r / eps_r);
+  if (arith == FOSB_ASM_FF && std::max(k0, k1) * mesh->d.diameter >= ff_max_phase())
+    return fail(FOSB_ERR_INVALID_ARG, "fosb_assemble_pmchwt: max(k0, k1) * mesh diameter = " +
+                                          std::to_string(std::max(k0, k1) * mesh->d.diameter) +
+                                          " exceeds the float-float phase range " + std::to_string(ff_max_phase()) +
+                                          "; use FOSB_ASM_FP64");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* z = static_cast<double*>(Z);
   double* z11 = z;
   double* z12 = z + 2 * N;
   double* z22 = z + 2 * (N * ldz + N);
   FOSB_CUDA(cudaMemset2DAsync(Z, ldz * 16, 0, 2 * N * 16, 2 * N, s));
-  FOSB_CUDA(assemble_pmchwt_one_k(mesh->d, k0, nss, z12, z11, ldz, s));
-  FOSB_CUDA(assemble_pmchwt_one_k(mesh->d, k1, nss, z22, z11, ldz, s));
+  FOSB_CUDA(assemble_pmchwt_one_k(mesh->d, k0, nss, arith, z12, z11, ldz, s));
+  FOSB_CUDA(assemble_pmchwt_one_k(mesh->d, k1, nss, arith, z22, z11, ldz, s));
   pmchwt_combine_kernel<<<pm_blocks(N * N, 256), 256, 0, s>>>(N, eta, static_cast<double2*>(Z), ldz);
   FOSB_CUDA(launched());
   if (n_inc > 0) {

@@ -51,9 +51,11 @@ MESHES = {
 }
 
 
+@pytest.mark.parametrize("arith", ["ASM_FP64", "ASM_FF"])
 @pytest.mark.parametrize("name,k0,er,mr,nss", [("ico1", 2.0, 2.1, 1.0, 5), ("ico2", 3.0, 2.1, 1.0, 5),
                                                ("torus20x8", 1.5, 2.0, 1.5, 3), ("ellipsoid2", 2.5, 4.0, 1.0, 5)])
-def test_pmchwt_assembly_matches_oracle(name, k0, er, mr, nss):
+def test_pmchwt_assembly_matches_oracle(name, k0, er, mr, nss, arith):
+    """Regular pairs in FP64 or float-float (FP32 pipe), touching pairs in FP64."""
     sm = MESHES[name]()
     m, om = _mesh(sm)
     N = m.n_edges
@@ -62,7 +64,7 @@ def test_pmchwt_assembly_matches_oracle(name, k0, er, mr, nss):
     Zbuf = torch.full((2 * N, 2 * N + 3), 7.0, dtype=C128, device=DEV)
     bbuf = torch.full((2 * N, 3), 7.0, dtype=C128, device=DEV)
     Z, b = Zbuf[:, :2 * N], bbuf[:, :2]
-    F.assemble_pmchwt(m, k0, er, mr, Z, inc=inc, b=b, n_ss=nss)
+    F.assemble_pmchwt(m, k0, er, mr, Z, inc=inc, b=b, n_ss=nss, arith=getattr(F, arith))
     Zo = O.assemble_pmchwt(om, k0, er, mr, n_ss=nss)
     bo = O.rhs_pmchwt(om, k0, inc[:, :3], inc[:, 3:6] + 1j * inc[:, 6:9])
     Zg, bg = Z.cpu().numpy(), b.cpu().numpy()
@@ -126,10 +128,10 @@ def test_pmchwt_accumulating_farfield_and_weights():
 
 def test_pmchwt_fullsize_sampled_entries_and_solve():
     """The benchmark's launch configuration: icosphere of 5120 triangles (2N = 15360),
-    k0 = 3, eps_r = 2.1; 400 sampled entries per block (random, plus the touching pairs of
-    the sample rows) against the oracle's entry-by-entry assembly at 1e-12 of max|Z|; b
-    against the oracle; the MIXED refined solve's backward error; the far field against
-    the Mie series (discretisation level)."""
+    k0 = 3, eps_r = 2.1, float-float regular pairs; 400 sampled entries per block (random,
+    plus the touching pairs of the sample rows) against the oracle's entry-by-entry
+    assembly at 1e-12 of max|Z|; b against the oracle; the MIXED refined solve's backward
+    error; the far field against the Mie series (discretisation level)."""
     sm = S.icosphere(4)
     m, om = _mesh(sm)
     N = m.n_edges
@@ -137,7 +139,7 @@ def test_pmchwt_fullsize_sampled_entries_and_solve():
     inc = F.incidence([[1.0, 0, 0]], [[0, 0, 1.0]])
     Z = torch.zeros((2 * N, 2 * N), dtype=C128, device=DEV)
     b = torch.zeros((2 * N, 1), dtype=C128, device=DEV)
-    F.assemble_pmchwt(m, k0, er, mr, Z, inc=inc, b=b)
+    F.assemble_pmchwt(m, k0, er, mr, Z, inc=inc, b=b, arith=F.ASM_FF)
     zmax = Z.abs().max().item()
     rng = np.random.default_rng(20230801)
     rows, cols = [], []
@@ -182,6 +184,10 @@ def test_pmchwt_argument_errors():
         # ldz < 2N (a view of Z would keep Z's row stride, so a narrower buffer)
         F.assemble_pmchwt(m, 2.0, 2.0, 1.0, torch.zeros((2 * N, 2 * N - 1), dtype=C128, device=DEV))
     assert e.value.status == F.FOSB_ERR_INVALID_ARG
+    for k0, arith in ((2.0, F.ASM_FP32), (30.0, F.ASM_FF)):   # no FP32 path; float-float phase range
+        with pytest.raises(F.FosbError) as e:
+            F.assemble_pmchwt(m, k0, 2.0, 1.0, Z, arith=arith)
+        assert e.value.status == F.FOSB_ERR_INVALID_ARG
     with pytest.raises(F.FosbError) as e:
         F.assemble_pmchwt(m, 2.0, 2.0, 1.0, Z, inc=F.incidence([[0, 0, 1.0]], [[np.nan, 0, 0]]),
                           b=torch.zeros((2 * N, 1), dtype=C128, device=DEV))
