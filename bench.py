@@ -52,6 +52,12 @@ WORKLOADS = {
     # l = 0.3), of the 1280-triangle sphere (N = 1920), k = 4, d = +z, p = x, 181 H-plane angles
     "mc-sphere-ka4-N1920-M512": dict(kind="mc", level=3, nsamp=512, k=4.0, sigma=0.005, ell=0.3, n_dir=181,
                                      d=(0, 0, 1), p=(1, 0, 0), seed=230801457),
+    # Monte Carlo for the dielectric sphere of Section V-A (k0 = 3, eps_r = 2.1, d = x, p = z):
+    # 128 sample surfaces of the 1280-triangle sphere (2N = 3840), each solved by the PMCHWT
+    # system; Gaussian sigma = 0.005, l = 0.3; 181 angles in the z = 0 plane
+    "mc-dielectric-sphere-k3-N3840-M128": dict(kind="mc", level=3, nsamp=128, k=3.0, sigma=0.005, ell=0.3,
+                                               n_dir=181, d=(1, 0, 0), p=(0, 0, 1), seed=230801457, eps_r=2.1,
+                                               mu_r=1.0, dirs="zplane"),
     # low-rank right-hand side (Section VI): the full tensor of one level (L0 = L = 3: the
     # 5120-triangle sphere, N = 7680, V = 2562), k = 4, Gaussian sigma = 0.005, l = 0.3, 181
     # H-plane angles; the kernel factored by pivoted Cholesky to a relative trace error of
@@ -526,10 +532,11 @@ def run_mc(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     W = WORKLOADS[args.workload]
     sm = S.icosphere(W["level"])
-    dirs = S.hplane_directions(W["n_dir"])
+    dirs = S.zplane_directions(W["n_dir"]) if W.get("dirs") == "zplane" else S.hplane_directions(W["n_dir"])
     z = S.gaussian_field_samples(W["nsamp"], sm.verts.shape[0], seed=W["seed"])
     prob = MonteCarloProblem(sm, W["k"], W["d"], W["p"], dirs, z, F.COV_GAUSS, W["sigma"], W["ell"], 1.0,
-                             workers=args.workers).setup()
+                             workers=args.workers, eps_r=W.get("eps_r"), mu_r=W.get("mu_r", 1.0),
+                             arith=F.ASM_FF if args.arith == "ff" else F.ASM_FP64).setup()
     for _ in range(args.warmup):
         out = prob.run()
     torch.cuda.synchronize()
@@ -557,7 +564,9 @@ def run_mc(args):
             "dtype": "mixed: float-float regular pairs, f64 singular pairs, 3xTF32 LU with FP64-class refinement",
             "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "samples": W["nsamp"], "k": W["k"], "n_dir": W["n_dir"],
-                       "sigma": W["sigma"], "ell": W["ell"], "parallelism": f"replicas{ws}"},
+                       "sigma": W["sigma"], "ell": W["ell"], "scatterer": "PEC" if W.get("eps_r") is None else
+                       f"dielectric eps_r = {W['eps_r']}, mu_r = {W.get('mu_r', 1.0)} (PMCHWT, 2N unknowns)",
+                       "parallelism": f"replicas{ws}"},
             "samples_per_s": round(W["nsamp"] / (ms * 1e-3), 1), "gpu_launches": launches, "clocks": clk,
             "variance_far_field_max": float(np.diag(out[2].cpu().numpy()).real.max())}
     if not args.no_cpu_baseline:
@@ -567,7 +576,11 @@ def run_mc(args):
         om = O.from_synth(sm)
         nsub = 8
         t = time.perf_counter()
-        O.monte_carlo(om, W["k"], W["d"], W["p"], dirs, "gauss", W["sigma"], W["ell"], 1.0, z[:nsub])
+        if W.get("eps_r") is None:
+            O.monte_carlo(om, W["k"], W["d"], W["p"], dirs, "gauss", W["sigma"], W["ell"], 1.0, z[:nsub])
+        else:
+            O.monte_carlo_dielectric(om, W["k"], W["eps_r"], W.get("mu_r", 1.0), W["d"], W["p"], dirs, "gauss",
+                                     W["sigma"], W["ell"], 1.0, z[:nsub])
         dt = time.perf_counter() - t
         line["cpu_baseline"] = {"value": round(dt / (nsub + 1) * (W["nsamp"] + 1), 2), "unit": "s per Monte Carlo run",
                                 "cores": len(os.sched_getaffinity(0)), "kind": "oracle",

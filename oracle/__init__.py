@@ -521,6 +521,26 @@ def monte_carlo(mesh: RWGMesh, k: float, d, p, xhat, kind: str, sigma: float, el
     return F0, Fs, D.T @ D.conj() / S, D.T @ D / S
 
 
+def monte_carlo_dielectric(mesh: RWGMesh, k0: float, eps_r: float, mu_r: float, d, p, xhat, kind: str,
+                           sigma: float, ell: float, t: float, z):
+    """The Monte Carlo estimator of Section V-C for a dielectric scatterer: the sample surfaces
+    of monte_carlo (xi = L z, L L^T = K + 1e-12 sigma^2 I), each solved by the PMCHWT system
+    (dielectric_farfield: assembly, LAPACK solve, far field of the exterior Cauchy data).
+    Returns (F0, F_s (S x 3 n_dir), (1/S) sum D D^H, (1/S) sum D D^T), D_s = (F_s - F0)/t."""
+    K = cov_kernel(mesh.verts, mesh.verts, kind, sigma, ell) + 1e-12 * sigma**2 * np.eye(mesh.nv)
+    xi = np.asarray(z, dtype=np.float64) @ np.linalg.cholesky(K).T
+
+    def far(verts):
+        m = RWGMesh(verts, mesh.tris, mesh.vnormals)
+        return dielectric_farfield(m, k0, eps_r, mu_r, d, p, xhat)[3].reshape(-1)
+
+    F0 = far(mesh.verts)
+    Fs = np.stack([far(mesh.verts + t * x[:, None] * mesh.vnormals) for x in xi])
+    D = (Fs - F0[None]) / t
+    S = Fs.shape[0]
+    return F0, Fs, D.T @ D.conj() / S, D.T @ D / S
+
+
 # ---------------------------------------------------------------------------
 # Shape derivatives of the discrete quantities (forward mode, efie_oracle_grad.cpp)
 # ---------------------------------------------------------------------------

@@ -84,3 +84,22 @@ def test_monte_carlo_approaches_first_order_covariance(F):
     var_rel = np.linalg.norm(np.diag(cov_mc).real - np.diag(cov).real) / np.linalg.norm(np.diag(cov).real)
     assert var_rel < 0.35, var_rel
     assert _rel(cov_mc, cov) < 0.4
+
+
+def test_dielectric_monte_carlo_matches_oracle_on_the_same_draws(F):
+    """A dielectric sphere (eps_r = 2.1): every sample surface solved by the PMCHWT system in
+    float-float assembly and MIXED solves, against the oracle's LAPACK solves on the same draws."""
+    from paper_2308_01457_gb300.montecarlo import MonteCarloProblem
+
+    sm = S.icosphere(2)
+    k, er, sig, ell, t = 2.0, 2.1, 1.0, 0.5, 1e-3
+    xh = S.hplane_directions(19)
+    z = S.gaussian_field_samples(8, sm.verts.shape[0], seed=13)
+    mc = MonteCarloProblem(sm, k, (0, 0, 1), (1, 0, 0), xh, z, F.COV_GAUSS, sig, ell, t, chunk=3,
+                           eps_r=er).setup()
+    F0, mean, cov, pcov = (x.cpu().numpy() for x in mc.run())
+    F0o, Fso, covo, pcovo = O.monte_carlo_dielectric(O.from_synth(sm), k, er, 1.0, [0, 0, 1], [1, 0, 0], xh, "gauss",
+                                                     sig, ell, t, z)
+    assert _rel(F0, F0o) < 1e-8
+    assert _rel(mean, Fso.mean(axis=0)) < 1e-8
+    assert _rel(cov, covo) < 1e-8 and _rel(pcov, pcovo) < 1e-8

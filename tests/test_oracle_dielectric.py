@@ -182,3 +182,36 @@ def test_mfio_identical_pairs_vanish(oracle_mod):
     ref = np.abs(O.mfio_block(m, k, 0, 1)).max() + np.abs(O.mfio_block(m, k, 0, 5)).max()
     for t in (0, 7, 33):
         assert np.abs(O.mfio_block(m, k, t, t)).max() < 1e-14 * ref
+
+
+def test_dielectric_monte_carlo_is_first_order_in_t(oracle_mod):
+    """The dielectric Monte Carlo (Section V-C) on fixed draws: its scaled deviations
+    D_s = (F_s - F0)/t tend to the linearised response G xi_s (G by central differences of
+    the PMCHWT far field along each draw, step 1e-4) at first order in t, so halving t
+    halves the gap; the sample covariance is Hermitian and positive semi-definite."""
+    sm = S.icosphere(1)
+    m = O.from_synth(sm)
+    k0, er, mr = 2.0, 2.1, 1.0
+    xh = S.hplane_directions(7)
+    d, p = [0, 0, 1], [1, 0, 0]
+    z = S.gaussian_field_samples(3, m.nv, seed=11)
+    sig, ell = 0.05, 0.5
+    K = O.cov_kernel(m.verts, m.verts, "gauss", sig, ell) + 1e-12 * sig**2 * np.eye(m.nv)
+    xi = z @ np.linalg.cholesky(K).T
+
+    def far(v):
+        return O.dielectric_farfield(O.RWGMesh(v, m.tris, m.vnormals), k0, er, mr, d, p, xh)[3].reshape(-1)
+
+    h = 1e-4
+    lin = np.stack([(far(m.verts + h * x[:, None] * m.vnormals) - far(m.verts - h * x[:, None] * m.vnormals)) / (2 * h)
+                    for x in xi])
+    gaps = []
+    for t in (0.02, 0.01):
+        F0, Fs, cov, pcov = O.monte_carlo_dielectric(m, k0, er, mr, d, p, xh, "gauss", sig, ell, t, z)
+        D = (Fs - F0[None]) / t
+        gaps.append(np.linalg.norm(D - lin) / np.linalg.norm(lin))
+        assert np.abs(cov - cov.conj().T).max() < 1e-12 * np.abs(cov).max()
+        assert np.linalg.eigvalsh(0.5 * (cov + cov.conj().T)).min() > -1e-10 * np.abs(cov).max()
+        assert np.abs(pcov - pcov.T).max() < 1e-12 * np.abs(pcov).max()
+    assert gaps[0] < 0.05, gaps
+    assert 1.6 < gaps[0] / gaps[1] < 2.4, gaps
