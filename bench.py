@@ -52,6 +52,11 @@ WORKLOADS = {
     # l = 0.3), of the 1280-triangle sphere (N = 1920), k = 4, d = +z, p = x, 181 H-plane angles
     "mc-sphere-ka4-N1920-M512": dict(kind="mc", level=3, nsamp=512, k=4.0, sigma=0.005, ell=0.3, n_dir=181,
                                      d=(0, 0, 1), p=(1, 0, 0), seed=230801457),
+    # the CT check of Section V-A on the dielectric sphere (k0 = 3, eps_r = 2.1, d = x, p = z,
+    # 1801 angles in the z = 0 plane): rank-one tensor right-hand side f (x) f over icosphere
+    # levels 0..3 (80 .. 5120 triangles, 2N = 240 .. 15360), L0 = 0, L = 3
+    "ct-dielectric-sphere-k3-L3": dict(kind="dect", levels=[0, 1, 2, 3], k=3.0, eps_r=2.1, mu_r=1.0, n_dir=1801,
+                                       d=(1, 0, 0), p=(0, 0, 1), L0=0, L=3),
     # Monte Carlo for the dielectric sphere of Section V-A (k0 = 3, eps_r = 2.1, d = x, p = z):
     # 128 sample surfaces of the 1280-triangle sphere (2N = 3840), each solved by the PMCHWT
     # system; Gaussian sigma = 0.005, l = 0.3; 181 angles in the z = 0 plane
@@ -887,6 +892,113 @@ def run_pmchwt(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dect(args):
+    """The dielectric CT workload: one step = every level's PMCHWT solve and far field
+    (DielectricCT.farfield) and the CT second moment of the rank-one right-hand side."""
+    import torch
+
+    import fosb_synth as S
+    import paper_2308_01457_gb300 as F
+    from paper_2308_01457_gb300.dielectric import DielectricCT
+
+    F.build.build()
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    sms = {l: S.icosphere(l + 1) for l in W["levels"]}
+    dirs = S.zplane_directions(W["n_dir"])
+    arith = F.ASM_FF if args.arith == "ff" else F.ASM_FP64
+    prob = DielectricCT(sms, W["k"], W["eps_r"], W["mu_r"], [W["d"]], [W["p"]], dirs, W["L0"], W["L"], arith=arith,
+                        device=f"cuda:{local}").setup()
+    for _ in range(args.warmup):
+        prob.run()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = F.lib().fosb_kernel_launches()
+    clocks = _clock_sampler(local) if rank == 0 else None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record()
+    for i in range(args.steps):
+        FL, M = prob.run()
+        ev[i + 1].record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = _clock_summary(clocks)
+    launches = int(F.lib().fosb_kernel_launches() - launches0)
+    ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]) / args.steps, ws, "cuda")
+    if rank != 0:
+        return
+    import oracle.mie as mie
+
+    R = np.array([[0, 0, 1.0], [0, -1.0, 0], [1.0, 0, 0]])  # (e_x, e_y, e_z) -> (e_z, -e_y, e_x)
+    Fz = (mie.farfield(W["k"], 1.0, dirs @ R, eps_r=W["eps_r"], mu_r=W["mu_r"]) @ R.T)[:, 2]
+    zz = torch.arange(2, 3 * W["n_dir"], 3, device=M.device)
+    Mz = M[zz][:, zz].cpu().numpy()
+    Mex = np.outer(Fz, Fz.conj())
+    FLz = FL.cpu().numpy()[2::3]
+    ex = None
+    if not args.no_e2e:
+        # the public API from host arrays: every level's mesh uploaded, the step, M downloaded
+        h2d = sum(sm.verts.nbytes + sm.tris.nbytes + sm.vnormals.nbytes for sm in sms.values())
+        ts = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = DielectricCT(sms, W["k"], W["eps_r"], W["mu_r"], [W["d"]], [W["p"]], dirs, W["L0"], W["L"],
+                              arith=arith, device=f"cuda:{local}").setup()
+            _, M2 = p2.run()
+            Mh = M2.cpu().numpy()
+            ts.append(time.perf_counter() - t0)
+            del p2, M2
+        ex = {"value": round(statistics.median(ts), 4), "unit": "s per CT step", "h2d_bytes_per_step": int(h2d),
+              "d2h_bytes_per_step": int(Mh.nbytes), "steps": 2, "stat": "median"}
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s per CT step", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: float-float (f32x2) regular pairs, f64 singular pairs, 3xTF32 tensor-core LU with "
+                     "FP64-class refinement", "data": "synthetic",
+            "config": {"workload": args.workload, "levels": W["levels"],
+                       "unknowns": [2 * prob.meshes[l].n_edges for l in W["levels"]], "k0": W["k"],
+                       "eps_r": W["eps_r"], "n_dir": W["n_dir"], "ct": [W["L0"], W["L"]], "assembly": args.arith,
+                       "parallelism": f"replicas{ws}"},
+            "rel_err_ct_second_moment_zz_vs_mie": float(np.linalg.norm(Mz - Mex) / np.linalg.norm(Mex)),
+            "rel_err_full_tensor_zz_vs_mie": float(np.linalg.norm(np.outer(FLz, FLz.conj()) - Mex) /
+                                                   np.linalg.norm(Mex)),
+            "ir_backward_error_max": max(prob.berr.values()), "gpu_launches": launches, "clocks": clk, "e2e": ex}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        lv = W["levels"]
+        t0 = time.perf_counter()
+        O.dielectric_ct_second_moment({l: O.from_synth(sms[l]) for l in lv[:-1]}, W["k"], W["eps_r"], W["mu_r"],
+                                      [W["d"]], [W["p"]], dirs, W["L0"], W["L"] - 1)
+        t_meas = time.perf_counter() - t0
+        om = O.from_synth(sms[lv[-2]])
+        t1 = time.perf_counter()
+        Zo = O.assemble_pmchwt(om, W["k"], W["eps_r"], W["mu_r"])
+        bo = O.rhs_pmchwt(om, W["k"], [W["d"]], [W["p"]])
+        t2 = time.perf_counter()
+        xo = O.solve(Zo, bo)
+        t3 = time.perf_counter()
+        O.farfield_matrix_pmchwt(om, W["k"], dirs) @ xo
+        t4 = time.perf_counter()
+        finest = (t2 - t1) * 16 + (t3 - t2) * 64 + (t4 - t3) * 4
+        line["cpu_baseline"] = {
+            "value": round(t_meas + finest, 2), "unit": "s per CT step", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": f"the oracle's CT step over levels {lv[0]}..{lv[-2]} measured end to end ({t_meas:.1f} s), plus "
+                      f"level {lv[-1]} from level {lv[-2]}'s measured phases scaled by the exact operation counts "
+                      f"(pairs x16, LU x64, far field x4: {finest:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batched(W):
     """The FP64 CPU oracle, as it stands, on the batched workload: assembly, plane-wave
     right-hand sides and the LAPACK solve of all 16 directions, measured for every
@@ -1202,7 +1314,7 @@ def main():
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     kind = WORKLOADS[args.workload].get("kind")
     if args.impl == "reference":
-        if kind in ("mc", "lowrank", "pmchwt"):
+        if kind in ("mc", "lowrank", "pmchwt", "dect"):
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the default workload; "
                               "this workload reports its oracle baseline in its own line"}))
         else:
@@ -1215,6 +1327,8 @@ def main():
         run_lowrank(args)
     elif kind == "pmchwt":
         run_pmchwt(args)
+    elif kind == "dect":
+        run_dect(args)
     else:
         run_fosb(args)
 

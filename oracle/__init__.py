@@ -521,6 +521,28 @@ def monte_carlo(mesh: RWGMesh, k: float, d, p, xhat, kind: str, sigma: float, el
     return F0, Fs, D.T @ D.conj() / S, D.T @ D / S
 
 
+def ct_second_moment_rank1(F: dict, L0: int, L: int) -> np.ndarray:
+    """Combination-technique second moment of a rank-one tensor right-hand side (Section V-A):
+    with M^2[f] = f (x) f the block system (Z_l1 (x) conj Z_l2) Sigma = f_l1 f_l2^H is solved by
+    Sigma_{l1,l2} = x_l1 x_l2^H, whose far field is F_l1 F_l2^H; the CT sums it with signs over
+    Lambda_+/- (Section IV-B), l1 >= l2 with the mirror.  F maps level -> far field vector."""
+    out = None
+    for (l1, l2), sgn in ct_hermitian_blocks(L0, L):
+        M = np.outer(F[l1], np.conj(F[l2]))
+        if l1 != l2:
+            M = M + M.conj().T
+        out = sgn * M if out is None else out + sgn * M
+    return out
+
+
+def dielectric_ct_second_moment(meshes: dict, k0: float, eps_r: float, mu_r: float, d, p, xhat, L0: int, L: int):
+    """Section V-A's check of the CT on the dielectric sphere: every level's PMCHWT far field
+    (dielectric_farfield, one plane wave) and the CT second moment of the rank-one right-hand
+    side.  meshes maps level -> RWGMesh.  Returns (second moment (3 n_dir)^2, {level: F_l})."""
+    F = {l: dielectric_farfield(meshes[l], k0, eps_r, mu_r, d, p, xhat)[3].reshape(-1) for l in range(L0, L + 1)}
+    return ct_second_moment_rank1(F, L0, L), F
+
+
 def monte_carlo_dielectric(mesh: RWGMesh, k0: float, eps_r: float, mu_r: float, d, p, xhat, kind: str,
                            sigma: float, ell: float, t: float, z):
     """The Monte Carlo estimator of Section V-C for a dielectric scatterer: the sample surfaces

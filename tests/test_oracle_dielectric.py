@@ -215,3 +215,26 @@ def test_dielectric_monte_carlo_is_first_order_in_t(oracle_mod):
         assert np.abs(pcov - pcov.T).max() < 1e-12 * np.abs(pcov).max()
     assert gaps[0] < 0.05, gaps
     assert 1.6 < gaps[0] / gaps[1] < 2.4, gaps
+
+
+def test_dielectric_ct_second_moment_converges_like_the_full_tensor(oracle_mod):
+    """Section V-A: the dielectric unit sphere (k0 = 3, eps_r = 2.1, d = x, p = z) with the
+    rank-one tensor right-hand side f (x) f, whose exact second moment is xi (x) xi: the CT
+    second moment of the far field's z component converges to the Mie series' F_z (x) conj F_z
+    at the full tensor's rate (within a factor 2 of its error), and L0 = L is the full tensor."""
+    k0, er = 3.0, 2.1
+    xh = S.zplane_directions(91)
+    R = np.array([[0, 0, 1.0], [0, -1.0, 0], [1.0, 0, 0]])
+    Fz = (mie.farfield(k0, 1.0, xh @ R, eps_r=er) @ R.T)[:, 2]
+    Mex = np.outer(Fz, Fz.conj())
+    meshes = {l: O.from_synth(S.icosphere(l + 1)) for l in range(3)}
+    M, F = O.dielectric_ct_second_moment(meshes, k0, er, 1.0, [[1.0, 0, 0]], [[0, 0, 1.0]], xh, 0, 2)
+    zz = np.arange(2, 3 * len(xh), 3)
+    ct = lambda L0, L: O.ct_second_moment_rank1(F, L0, L)[np.ix_(zz, zz)] if (L0, L) != (0, 2) else M[np.ix_(zz, zz)]
+    err = lambda A: np.linalg.norm(A - Mex) / np.linalg.norm(Mex)
+    full = {L: np.outer(F[L], F[L].conj())[np.ix_(zz, zz)] for L in range(3)}
+    assert np.abs(ct(2, 2) - full[2]).max() == 0.0
+    e_ct = [err(ct(0, L)) for L in (1, 2)]
+    assert e_ct[0] / e_ct[1] > 2.5, e_ct
+    assert e_ct[1] < 2.0 * err(full[2]), (e_ct, err(full[2]))
+    assert np.abs(M - M.conj().T).max() < 1e-14 * np.abs(M).max()
