@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(128) efie_regular_ff_kernel(DevMesh m, FFConst
 }
 
 // Dielectric (PMCHWT) system: the EFIO block into ZT and the MFIO block into ZK.
-__global__ void __launch_bounds__(128) pmchwt_regular_ff_kernel(DevMesh m, FFConst C, double* ZT, double* ZK,
+__global__ void __launch_bounds__(128, 3) pmchwt_regular_ff_kernel(DevMesh m, FFConst C, double* ZT, double* ZK,
                                                                 int64_t ldz) {
   __shared__ float tab[128][4];
   for (int e = threadIdx.x; e < 128 * 4; e += blockDim.x) tab[e >> 2][e & 3] = c_sctab[e >> 2][e & 3];
