@@ -16,7 +16,9 @@
  *     CTsubsystem) with C = E[g g^H] built from the PEC shape-derivative right-hand
  *     side g of Section III (eq. secondPEC);
  *   - far-field and RCS moments (Section II-C, the far-field expansion and eq. RCS),
- *     combined over the combination-technique index sets Lambda_+/- (Section IV-B).
+ *     combined over the combination-technique index sets Lambda_+/- (Section IV-B);
+ *   - for a dielectric scatterer, the PMCHWT system of Section II-C (eq. pmchwt) and its
+ *     far field (fosb_assemble_pmchwt, fosb_farfield_pmchwt).
  *
  * Conventions (every call):
  *   - Complex arrays are interleaved (re, im): complex128 = 2 doubles, complex64 =
