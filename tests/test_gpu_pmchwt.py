@@ -210,3 +210,34 @@ def test_dielectric_ct_second_moment_matches_oracle():
     assert _rel(FL, Fo[2]) < 1e-8
     assert _rel(M, Mo) < 1e-8
     assert max(prob.berr.values()) <= max(64.0, 8.0 * math.sqrt(2 * 1920)) * 2.0**-52
+
+
+def _closed_polyhedron(verts, tris):
+    """Triangles oriented counter-clockwise seen from outside (normal . centroid > 0)."""
+    verts = np.asarray(verts, dtype=np.float64)
+    out = []
+    for t in tris:
+        a, b, c = verts[list(t)]
+        n = np.cross(b - a, c - a)
+        out.append(list(t) if np.dot(n, a + b + c) > 0 else [t[0], t[2], t[1]])
+    vn = verts / np.linalg.norm(verts, axis=1, keepdims=True)
+    return S.SurfaceMesh(verts, np.asarray(out, dtype=np.int32), vn)
+
+
+@pytest.mark.parametrize("arith", ["ASM_FP64", "ASM_FF"])
+def test_pmchwt_degenerate_meshes(arith):
+    """Edge cases: a tetrahedron (every triangle pair touches, so the regular-pair launches add
+    nothing) and an octahedron (vertex-disjoint pairs only between opposite faces), with no
+    incident data (b NULL): the matrix against the oracle at 1e-12."""
+    tet = _closed_polyhedron([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]],
+                             [[0, 1, 2], [0, 1, 3], [0, 2, 3], [1, 2, 3]])
+    octa = _closed_polyhedron([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]],
+                              [[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4], [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]])
+    for sm in (tet, octa):
+        m, om = _mesh(sm)
+        N = m.n_edges
+        Z = torch.full((2 * N, 2 * N), 3.0, dtype=C128, device=DEV)
+        F.assemble_pmchwt(m, 1.5, 2.1, 1.2, Z, arith=getattr(F, arith))
+        Zo = O.assemble_pmchwt(om, 1.5, 2.1, 1.2)
+        assert np.abs(Z.cpu().numpy() - Zo).max() <= 1e-12 * np.abs(Zo).max()
+
