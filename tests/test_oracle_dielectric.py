@@ -238,3 +238,26 @@ def test_dielectric_ct_second_moment_converges_like_the_full_tensor(oracle_mod):
     assert e_ct[0] / e_ct[1] > 2.5, e_ct
     assert e_ct[1] < 2.0 * err(full[2]), (e_ct, err(full[2]))
     assert np.abs(M - M.conj().T).max() < 1e-14 * np.abs(M).max()
+
+
+def test_pmchwt_discrete_reciprocity(oracle_mod):
+    """Reciprocity of the scattering amplitude, p2 . F(-d2; d1, p1) = p1 . F(-d1; d2, p2), holds
+    for the discrete PMCHWT solution to rounding (on an ellipsoid, two oblique waves,
+    mu_r != 1).  It fixes the conventions of the incident data (the d x p block) and of the
+    far field of (j, m), which the Mie pins see only through a symmetric sphere."""
+    m = O.from_synth(S.ellipsoid(1, (0.6, 1.3, 0.9)))
+    k0, er, mr = 2.0, 2.1, 1.3
+    d1 = np.array([0.3, 0.4, math.sqrt(0.75)])
+    d1 /= np.linalg.norm(d1)
+    d2 = np.array([-0.5, 0.7, 0.2])
+    d2 /= np.linalg.norm(d2)
+    p1 = np.cross(d1, [0, 0, 1.0])
+    p1 /= np.linalg.norm(p1)
+    p2 = np.cross(d2, [1.0, 0, 0])
+    p2 /= np.linalg.norm(p2)
+    Z = O.assemble_pmchwt(m, k0, er, mr)
+    b = O.rhs_pmchwt(m, k0, np.stack([d1, d2]), np.stack([p1, p2]).astype(complex))
+    x = O.solve(Z, b)
+    A = O.farfield_matrix_pmchwt(m, k0, np.stack([-d2, -d1]))
+    a, c = p2 @ (A[0:3] @ x[:, 0]), p1 @ (A[3:6] @ x[:, 1])
+    assert abs(a - c) < 1e-12 * abs(a), (a, c)
