@@ -19,6 +19,9 @@
 // wavenumbers, T_0 into the (1,2) block and T_1, as scratch, into the (2,2) block.  A final
 // pass rewrites every entry: (1,2) = T_0 + eta T_1, (2,1) = -T_0 - T_1/eta, (2,2) = (1,1).
 // So a triangle pair costs 18 complex atomics per wavenumber, the same as the PEC EFIE.
+// The regular pairs run in FP64 here (FOSB_ASM_FP64) or in float-float on the FP32 pipe
+// (FOSB_ASM_FF, pmchwt_regular_ff_kernel in ff_assemble.cu, from barycentric moment
+// matrices); the touching pairs always run in FP64 here.
 //
 // Moments.  With x' = x - o1, y' = y - o2 (first vertices as origins) and D = o1 - o2,
 //   EFIO:  I0 = sum w G, X = sum w G x', Y = sum w G y', XY = sum w G x'.y',   G = exp(ikr)/r;
