@@ -301,6 +301,10 @@ def assemble_pmchwt(mesh: Mesh, k0: float, eps_r: float, mu_r: float, Z, inc=Non
     """fosb_assemble_pmchwt: the dielectric scatterer's PMCHWT matrix Z (2N x 2N complex128)
     and, if inc is given, the tested incident Cauchy data b (2N x n_inc); regular pairs in
     FP64 (ASM_FP64) or float-float (ASM_FF)."""
+    import torch
+
+    if Z.dtype != torch.complex128 or (b is not None and b.dtype != torch.complex128):
+        raise ValueError("assemble_pmchwt: Z and b must be complex128")
     opts = QuadOpts(n_ss, arith)
     inc_a = None if inc is None else _np(inc, np.float64).reshape(-1, 9)
     n_inc = 0 if inc_a is None else inc_a.shape[0]
@@ -313,6 +317,10 @@ def assemble_pmchwt(mesh: Mesh, k0: float, eps_r: float, mu_r: float, Z, inc=Non
 
 def farfield_pmchwt(mesh: Mesh, k0: float, dirs, X, out, weight: float = 1.0, accumulate: bool = False, stream=None):
     """fosb_farfield_pmchwt: out (3 n_dir x ncols) = w A X for exterior Cauchy data X (2N x ncols)."""
+    import torch
+
+    if X.dtype != torch.complex128 or out.dtype != torch.complex128:
+        raise ValueError("farfield_pmchwt: X and out must be complex128")
     d = _np(dirs, np.float64).reshape(-1, 3)
     ncols = 1 if X.dim() == 1 else X.shape[1]
     _check(lib().fosb_farfield_pmchwt(mesh.handle, ctypes.c_double(k0), d.ctypes.data_as(ctypes.c_void_p),
